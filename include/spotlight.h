@@ -1,0 +1,182 @@
+/*
+ * spotlight.h -- C ABI of libspotlight, the GB300 (sm_103a) search hot path
+ * of the SPOTLIGHT real-time transient pipeline (arXiv 2606.27262, Sec. 3.1):
+ * brute-force incoherent dedispersion of an 8-bit filterbank beam over a list
+ * of trial DMs, then a multi-width boxcar single-pulse search with per-block
+ * mean/sigma normalisation, a threshold and a 3x3 peak filter that emit a
+ * candidate list.
+ *
+ * Conventions shared by every call
+ *   - All functions return SP_OK (0) or a negative SP_E* code; sp_strerror()
+ *     names it.  Arguments are checked on the host before anything is
+ *     launched; a failed check launches nothing and writes nothing.
+ *   - "d_" pointers are device pointers (memory of the current CUDA device),
+ *     "h_" pointers are host pointers.  The caller owns every buffer it
+ *     passes; the library keeps no pointer to them after the call returns.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     work is enqueued on it and the call returns without waiting, except
+ *     where a call says it synchronises.  Buffers must stay valid until the
+ *     stream has executed the work.
+ *   - Only sp_plan_create and sp_searcher_create allocate device memory; the
+ *     other calls allocate nothing.  Calls on different streams may overlap
+ *     as long as they do not share output or workspace buffers.
+ *   - Filterbank layout: uint8 [n_in][nchan], time-major (the order a
+ *     filterbank file or ring block stores samples), channel 0 = the highest
+ *     frequency (the band is flipped highest-first, Sec. 2).
+ *   - DM-transform layout: int32 [ndm][n_out], row d = trial DM d.
+ */
+#ifndef SPOTLIGHT_H
+#define SPOTLIGHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SP_OK 0
+#define SP_EINVAL (-1)     /* invalid argument (null pointer, bad value)      */
+#define SP_ESHAPE (-2)     /* sizes inconsistent (n_in < n_out + max delay)   */
+#define SP_ECUDA (-3)      /* a CUDA runtime call failed                      */
+#define SP_EOVERFLOW (-4)  /* more candidates than the caller's capacity      */
+#define SP_ENOMEM (-5)     /* device or host allocation failed                */
+#define SP_EWORKSPACE (-6) /* workspace pointer null or too small             */
+#define SP_ELIMIT (-7)     /* a size is beyond a documented library limit     */
+
+/* Library limits. */
+#define SP_MAX_WIDTHS 16        /* trial boxcar widths per search           */
+#define SP_MAX_WIDTH 1024       /* largest trial boxcar width, samples      */
+
+typedef struct sp_plan sp_plan;
+typedef struct sp_searcher sp_searcher;
+
+/* One single-pulse candidate (Sec. 3.1.2): trial-DM row, first sample of the
+ * boxcar window [t, t + w), index of the best width in the caller's width
+ * list, and that width's S/N. */
+typedef struct {
+    int32_t dm_idx;
+    int32_t t;
+    int32_t width_idx;
+    float snr;
+} sp_cand;
+
+const char *sp_strerror(int code);
+
+/* ------------------------------------------------------------------ plan --
+ * Dedispersion plan (Sec. 3.1.1).  For trial DM d and channel c the delay is
+ *   delay[d][c] = floor(x + 0.5),
+ *   x = 4.148808e3 * dms[d] * (1/freqs[c]^2 - 1/freqs[0]^2) / tsamp_s
+ * evaluated in IEEE binary64 from left to right (Eq. 1 with the highest
+ * frequency as reference; 4.148808e3 MHz^2 pc^-1 cm^3 s is Eq. 1's
+ * dispersion constant rounded).  The plan computes the table on the host,
+ * uploads it once and derives the DM-tile layout the kernels use.
+ *   freqs_mhz [nchan]  host, copied; > 0 and strictly decreasing.
+ *   dms [ndm]          host, copied; >= 0 (any order).
+ *   tsamp_s            sampling time, > 0.
+ *   out                receives a library-owned plan; free with sp_plan_destroy.
+ * Errors: SP_EINVAL for invalid values, SP_ELIMIT if a delay or a size does
+ * not fit int32, SP_ENOMEM / SP_ECUDA if the device upload fails.  Uses the
+ * current CUDA device; the plan must be used on that device only. */
+int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsamp_s,
+                   const double *dms, int32_t ndm, sp_plan **out);
+int sp_plan_destroy(sp_plan *plan);
+/* max_delay = the largest delay[d][c] (D_max, samples); any out pointer may
+ * be NULL. */
+int sp_plan_info(const sp_plan *plan, int32_t *max_delay, int32_t *nchan, int32_t *ndm);
+/* Copies the delay table, int32 [ndm][nchan], to host memory. */
+int sp_plan_delays(const sp_plan *plan, int32_t *h_out);
+/* The same delay table computed on the host only (no device, no plan):
+ * h_out [ndm][nchan] int32 and *max_delay (may be NULL).  Lets a caller size
+ * n_in = n_out + max_delay before touching a GPU.  Same errors as
+ * sp_plan_create's argument checks. */
+int sp_compute_delays(const double *freqs_mhz, int32_t nchan, double tsamp_s,
+                      const double *dms, int32_t ndm, int32_t *h_out, int32_t *max_delay);
+
+/* ----------------------------------------------------------- dedisperse --
+ * Brute-force incoherent dedispersion (Sec. 3.1.1, the DM transform):
+ *   d_out[d][t] = sum_{c < nchan} d_in[t + delay[d][c]][c],  0 <= t < n_out,
+ * exact in int32 (every sum is at most 255 * nchan).  The input must hold
+ * the overlap of the maximum sweep (Sec. 3.1 overlap-read):
+ * n_out = n_in - max_delay is required, else SP_ESHAPE.
+ *   d_in  [n_in][nchan] uint8, device, 16-byte aligned.
+ *   d_out [ndm][n_out]  int32, device.
+ *   d_work / work_bytes: device scratch of at least
+ *         sp_dedisperse_workspace_bytes(plan, n_in) bytes, 256-byte aligned
+ *         (holds a channel-major copy of the input); contents on entry are
+ *         ignored, on return undefined.
+ * Errors: SP_EINVAL, SP_ESHAPE, SP_EWORKSPACE, SP_ELIMIT, SP_ECUDA (launch). */
+int64_t sp_dedisperse_workspace_bytes(const sp_plan *plan, int64_t n_in);
+int sp_dedisperse(const sp_plan *plan, const uint8_t *d_in, int64_t n_in,
+                  int32_t *d_out, int64_t n_out, void *d_work, int64_t work_bytes,
+                  void *stream);
+
+/* ------------------------------------------------- single-pulse search --
+ * Boxcar matched-filter search of a DM transform (Sec. 3.1.2).
+ * Normalisation: each row is cut into nblk = max(1, n_out / norm_block)
+ * blocks [b*L, (b+1)*L) (the last also takes the remainder; norm_block <= 0
+ * or >= n_out means one block).  With n, Sx, Sxx the count, sum and sum of
+ * squares of block b (population variance), the S/N of the window [t, t+w)
+ * whose first sample t lies in block b is
+ *   snr_w(d, t) = (n*S - w*Sx) / (sqrt(w) * sqrt(n*Sxx - Sx^2)),
+ *   S = sum_{k<w} dmt[d][t+k]        (windows never cross n_out),
+ * and 0 for a zero-variance block.  best(d,t) is the maximum over the
+ * widths (smallest width index on ties); -inf where no width fits.
+ * A candidate is (d,t) with best(d,t) >= threshold that is a 3x3 local
+ * maximum of best in the DM-time plane: strictly greater than each in-range
+ * neighbour that precedes it in (d,t) order and >= each one after it.
+ *   d_dmt [ndm][n_out] int32 device.
+ *   h_widths [nw]      host, strictly increasing, 1..SP_MAX_WIDTH,
+ *                      nw <= SP_MAX_WIDTHS.
+ *   d_work/work_bytes  device scratch of sp_sps_workspace_bytes(...) bytes,
+ *                      256-byte aligned (per-row block statistics).
+ *   d_cands [cap]      device; receives min(count, cap) candidates in an
+ *                      unspecified order (sort by (dm_idx, t) for a
+ *                      canonical list).
+ *   d_count            device int64; receives the total number found, which
+ *                      exceeds cap on overflow (then only cap are written).
+ * S/N is evaluated in float32 from an exact integer numerator; it agrees
+ * with an exact evaluation to about 1e-6 relative.
+ * Errors: SP_EINVAL, SP_ELIMIT, SP_EWORKSPACE, SP_ECUDA. */
+int64_t sp_sps_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block);
+int sp_single_pulse_search(const int32_t *d_dmt, int32_t ndm, int64_t n_out,
+                           const int32_t *h_widths, int32_t nw, float threshold,
+                           int64_t norm_block, void *d_work, int64_t work_bytes,
+                           sp_cand *d_cands, int64_t cap, int64_t *d_count,
+                           void *stream);
+/* The map the candidates are picked from: d_best [ndm][n_out] float (best
+ * S/N, -inf where no width fits) and d_wbest [ndm][n_out] int8 (index of the
+ * best width, -1 where none fits).  Same arguments and arithmetic as
+ * sp_single_pulse_search. */
+int sp_best_snr_map(const int32_t *d_dmt, int32_t ndm, int64_t n_out,
+                    const int32_t *h_widths, int32_t nw, int64_t norm_block,
+                    void *d_work, int64_t work_bytes, float *d_best, int8_t *d_wbest,
+                    void *stream);
+
+/* -------------------------------------------------------------- searcher --
+ * The whole per-beam path -- dedispersion, normalisation, boxcars, 3x3
+ * peaks -- with every device buffer it needs allocated once up front, for a
+ * fixed plan, searched length n_out (n_in = n_out + max_delay), width list,
+ * threshold, normalisation block and candidate capacity.  The run calls
+ * allocate nothing.
+ * Errors from create: SP_EINVAL, SP_ELIMIT, SP_ENOMEM, SP_ECUDA. */
+int sp_searcher_create(const sp_plan *plan, int64_t n_out, const int32_t *h_widths,
+                       int32_t nw, float threshold, int64_t norm_block, int64_t cand_cap,
+                       sp_searcher **out);
+int sp_searcher_destroy(sp_searcher *s);
+/* Device-resident run: d_in [n_in][nchan] uint8 device (16-byte aligned),
+ * d_cands [cap] / d_count as in sp_single_pulse_search.  Asynchronous. */
+int sp_searcher_run(sp_searcher *s, const uint8_t *d_in, sp_cand *d_cands, int64_t cap,
+                    int64_t *d_count, void *stream);
+/* End-to-end run from host memory: copies h_in [n_in][nchan] to the device
+ * (page-locked memory makes this copy asynchronous and fast), searches,
+ * copies min(count, cap) candidates to h_cands and the total to *h_count,
+ * and synchronises the stream before returning.  Returns SP_EOVERFLOW
+ * (after filling h_cands) when the total exceeds min(cap, cand_cap). */
+int sp_searcher_run_host(sp_searcher *s, const uint8_t *h_in, sp_cand *h_cands, int64_t cap,
+                         int64_t *h_count, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPOTLIGHT_H */

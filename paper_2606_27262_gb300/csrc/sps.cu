@@ -1,0 +1,286 @@
+// sps.cu -- boxcar matched-filter single-pulse search on sm_103a
+// (arXiv 2606.27262, Sec. 3.1.2: boxcar templates of several trial widths as
+// differences of a running cumulative sum, S/N against per-block statistics,
+// a threshold, and a 3x3 peak filter in the DM-time plane).
+//
+// Kernels:
+//   sps_stats_kernel   one CTA per (row, normalisation block): exact int64
+//                      sum and sum of squares, the 128-bit variance term, and
+//                      per-width float coefficients of the S/N affine map.
+//   sps_boxcar_kernel  one CTA per 14 rows x 256 samples (+1 halo row and
+//                      sample on each side).  Stages int64 prefix sums of the
+//                      rows in shared memory (warp-shuffle scans), evaluates
+//                      every width for every (row, sample), keeps the best,
+//                      then applies the threshold and the 3x3 rule from the
+//                      staged best-S/N tile and appends candidates with one
+//                      atomic per warp.  A template switch writes the best-S/N
+//                      map instead of candidates.
+//
+// S/N arithmetic.  For block b of row d with count n, sum Sx, sum of squares
+// Sxx, let m0 = floor(Sx/n) and f = Sx/n - m0.  For a window sum S of width w
+//   snr = (n*S - w*Sx) / (sqrt(w)*sqrt(n*Sxx - Sx^2))
+//       = ((S - w*m0) - w*f) * inv_w,   inv_w = n / (sqrt(w)*sqrt(V)).
+// S - w*m0 is formed exactly in int64 from the prefix sums; only the final
+// conversion to float and one fused multiply-add round.
+#include <cmath>
+
+#include "sp_internal.h"
+
+namespace sp {
+namespace {
+
+struct WidthList {
+    int32_t w[SP_MAX_WIDTHS];
+    int32_t nw;
+};
+
+__device__ __forceinline__ int64_t warp_sum_i64(int64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restrict__ dmt, int64_t n_out,
+                                                        int64_t norm_block, int64_t nblk, WidthList wl,
+                                                        int32_t *__restrict__ m0_out,
+                                                        float2 *__restrict__ coef_out) {
+    __shared__ int64_t red1[8], red2[8];
+    const int64_t b = blockIdx.x;
+    const int64_t d = blockIdx.y;
+    const int64_t lo = (nblk == 1) ? 0 : b * norm_block;
+    const int64_t hi = (b == nblk - 1) ? n_out : (b + 1) * norm_block;
+    const int32_t *row = dmt + d * n_out;
+    int64_t s1 = 0, s2 = 0;
+    for (int64_t t = lo + threadIdx.x; t < hi; t += 256) {
+        const int64_t x = __ldg(row + t);
+        s1 += x;
+        s2 += x * x;
+    }
+    s1 = warp_sum_i64(s1);
+    s2 = warp_sum_i64(s2);
+    if ((threadIdx.x & 31) == 0) {
+        red1[threadIdx.x >> 5] = s1;
+        red2[threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t S1 = 0, S2 = 0;
+        for (int i = 0; i < 8; ++i) {
+            S1 += red1[i];
+            S2 += red2[i];
+        }
+        const int64_t n = hi - lo;
+        int64_t m0 = S1 / n;
+        if (S1 - m0 * n < 0) --m0;  // floor for negative sums
+        const double frac = (double)(S1 - m0 * n) / (double)n;
+        const __int128 var_n2 = (__int128)n * S2 - (__int128)S1 * S1;
+        const double inv_sigma = var_n2 > 0 ? (double)n / sqrt((double)var_n2) : 0.0;
+        const int64_t idx = d * nblk + b;
+        m0_out[idx] = (int32_t)m0;
+        for (int k = 0; k < wl.nw; ++k) {
+            const double w = (double)wl.w[k];
+            const double inv = inv_sigma / sqrt(w);
+            coef_out[idx * wl.nw + k] = make_float2((float)inv, (float)(w * frac * inv));
+        }
+    }
+}
+
+constexpr int kBxT = 256;                 // output samples per CTA
+constexpr int kBxRows = 16;               // staged rows: 14 interior + 2 halo
+constexpr int kBxIn = kBxRows - 2;
+constexpr int kBxTT = kBxT + 2;           // staged samples incl. halo
+constexpr int kBxPerLane = (kBxTT + 31) / 32;
+
+template <bool MAP>
+__global__ void __launch_bounds__(256, 2)
+sps_boxcar_kernel(const int32_t *__restrict__ dmt, int32_t ndm, int64_t n_out, WidthList wl, int32_t maxw,
+                  float thr, int64_t norm_block, int64_t nblk, const int32_t *__restrict__ m0s,
+                  const float2 *__restrict__ coefs, sp_cand *__restrict__ cands, int64_t cap,
+                  unsigned long long *__restrict__ count, float *__restrict__ map_best,
+                  int8_t *__restrict__ map_k) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int LP = kBxTT + maxw;  // prefix entries 0..LP
+    int64_t *P = reinterpret_cast<int64_t *>(smem);
+    float *snr_s = reinterpret_cast<float *>(smem + (size_t)kBxRows * (LP + 1) * 8);
+    int8_t *k_s = reinterpret_cast<int8_t *>(snr_s + kBxRows * kBxTT);
+
+    const int64_t t0 = (int64_t)blockIdx.x * kBxT;
+    const int64_t tbase = t0 - 1;
+    const int d0 = blockIdx.y * kBxIn;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // Phase 1: exclusive prefix sums P[r][i] = sum_{j<i} x(tbase + j).
+    for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
+        const int d = d0 - 1 + rr;
+        const bool rv = d >= 0 && d < ndm;
+        const int32_t *row = dmt + (int64_t)d * n_out;
+        int64_t *Pr = P + (size_t)rr * (LP + 1);
+        if (lane == 0) Pr[0] = 0;
+        int64_t carry = 0;
+        for (int base = 0; base < LP; base += 32) {
+            const int i = base + lane;
+            const int64_t t = tbase + i;
+            int64_t v = (rv && i < LP && t >= 0 && t < n_out) ? (int64_t)__ldg(row + t) : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (i < LP) Pr[i + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+
+    // Phase 2: best S/N over the widths for every staged (row, sample).
+    for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
+        const int d = d0 - 1 + rr;
+        const bool rv = d >= 0 && d < ndm;
+        const int64_t *Pr = P + (size_t)rr * (LP + 1);
+        int64_t cb = -1;
+        int64_t m0 = 0;
+        float2 cf[SP_MAX_WIDTHS];
+#pragma unroll
+        for (int k = 0; k < SP_MAX_WIDTHS; ++k) cf[k] = make_float2(0.f, 0.f);
+        for (int j = 0; j < kBxPerLane; ++j) {
+            const int ti = lane * kBxPerLane + j;
+            if (ti >= kBxTT) break;
+            const int64_t t = tbase + ti;
+            float best = -INFINITY;
+            int kb = -1;
+            if (rv && t >= 0 && t < n_out) {
+                int64_t b = (norm_block > 0) ? t / norm_block : 0;
+                if (b > nblk - 1) b = nblk - 1;
+                if (b != cb) {
+                    cb = b;
+                    const int64_t idx = (int64_t)d * nblk + b;
+                    m0 = __ldg(m0s + idx);
+#pragma unroll
+                    for (int k = 0; k < SP_MAX_WIDTHS; ++k)
+                        if (k < wl.nw) cf[k] = __ldg(coefs + idx * wl.nw + k);
+                }
+                const int64_t p0 = Pr[ti];
+#pragma unroll
+                for (int k = 0; k < SP_MAX_WIDTHS; ++k) {
+                    if (k < wl.nw) {
+                        const int w = wl.w[k];
+                        if (t + w <= n_out) {
+                            const int64_t x = Pr[ti + w] - p0 - (int64_t)w * m0;
+                            const float s = fmaf((float)x, cf[k].x, -cf[k].y);
+                            if (kb < 0 || s > best) {
+                                best = s;
+                                kb = k;
+                            }
+                        }
+                    }
+                }
+            }
+            snr_s[rr * kBxTT + ti] = best;
+            k_s[rr * kBxTT + ti] = (int8_t)kb;
+        }
+    }
+    __syncthreads();
+
+    // Phase 3: interior points -- map output, or threshold + 3x3 + append.
+    for (int idx = threadIdx.x; idx < kBxIn * kBxT; idx += 256) {
+        const int rr = 1 + idx / kBxT;
+        const int ti = 1 + idx % kBxT;
+        const int d = d0 - 1 + rr;
+        const int64_t t = tbase + ti;
+        const bool inr = d < ndm && t < n_out;
+        const float v = snr_s[rr * kBxTT + ti];
+        if (MAP) {
+            if (inr) {
+                map_best[(int64_t)d * n_out + t] = v;
+                map_k[(int64_t)d * n_out + t] = k_s[rr * kBxTT + ti];
+            }
+        } else {
+            bool cand = inr && v >= thr;
+            if (cand) {
+                const float *up = snr_s + (rr - 1) * kBxTT + ti;
+                const float *mid = snr_s + rr * kBxTT + ti;
+                const float *dn = snr_s + (rr + 1) * kBxTT + ti;
+                cand = v > up[-1] && v > up[0] && v > up[1] && v > mid[-1] && v >= mid[1] && v >= dn[-1] &&
+                       v >= dn[0] && v >= dn[1];
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, cand);
+            if (mask) {
+                const int leader = __ffs(mask) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (cand) {
+                    const unsigned long long pos = base + __popc(mask & ((1u << lane) - 1u));
+                    if ((int64_t)pos < cap) {
+                        sp_cand c;
+                        c.dm_idx = d;
+                        c.t = (int32_t)t;
+                        c.width_idx = k_s[rr * kBxTT + ti];
+                        c.snr = v;
+                        cands[pos] = c;
+                    }
+                }
+            }
+        }
+    }
+}
+
+size_t boxcar_smem(int maxw) {
+    return (size_t)kBxRows * (kBxTT + maxw + 1) * 8 + (size_t)kBxRows * kBxTT * 4 + (size_t)kBxRows * kBxTT;
+}
+
+}  // namespace
+
+int64_t sps_nblocks(int64_t n_out, int64_t norm_block) {
+    if (norm_block <= 0 || norm_block >= n_out) return 1;
+    const int64_t nb = n_out / norm_block;
+    return nb < 1 ? 1 : nb;
+}
+
+int64_t sps_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block) {
+    const int64_t nblk = sps_nblocks(n_out, norm_block);
+    return align256((int64_t)ndm * nblk * 4) + align256((int64_t)ndm * nblk * nw * 8);
+}
+
+int launch_sps(const SpsArgs &a, cudaStream_t stream) {
+    WidthList wl;
+    for (int k = 0; k < SP_MAX_WIDTHS; ++k) wl.w[k] = k < a.nw ? a.widths[k] : 0;
+    wl.nw = a.nw;
+    const int maxw = a.widths[a.nw - 1];
+    int32_t *m0s = reinterpret_cast<int32_t *>(a.work);
+    float2 *coefs = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(a.work) +
+                                               align256((int64_t)a.ndm * a.nblk * 4));
+    sps_stats_kernel<<<dim3((unsigned)a.nblk, (unsigned)a.ndm), 256, 0, stream>>>(a.dmt, a.n_out, a.norm_block,
+                                                                                a.nblk, wl, m0s, coefs);
+    if (cudaGetLastError() != cudaSuccess) return SP_ECUDA;
+
+    const size_t smem = boxcar_smem(maxw);
+    const dim3 grid((unsigned)((a.n_out + kBxT - 1) / kBxT), (unsigned)((a.ndm + kBxIn - 1) / kBxIn));
+    if (a.map_best) {
+        static size_t configured = 0;
+        if (configured < smem) {
+            if (cudaFuncSetAttribute(sps_boxcar_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return SP_ECUDA;
+            configured = smem;
+        }
+        sps_boxcar_kernel<true><<<grid, 256, smem, stream>>>(a.dmt, a.ndm, a.n_out, wl, maxw, a.threshold,
+                                                             a.norm_block, a.nblk, m0s, coefs, nullptr, 0,
+                                                             nullptr, a.map_best, a.map_wbest);
+    } else {
+        static size_t configured = 0;
+        if (configured < smem) {
+            if (cudaFuncSetAttribute(sps_boxcar_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return SP_ECUDA;
+            configured = smem;
+        }
+        if (cudaMemsetAsync(a.count, 0, sizeof(int64_t), stream) != cudaSuccess) return SP_ECUDA;
+        sps_boxcar_kernel<false><<<grid, 256, smem, stream>>>(
+            a.dmt, a.ndm, a.n_out, wl, maxw, a.threshold, a.norm_block, a.nblk, m0s, coefs, a.cands, a.cap,
+            reinterpret_cast<unsigned long long *>(a.count), nullptr, nullptr);
+    }
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+}  // namespace sp

@@ -1,0 +1,86 @@
+"""CPU-only checks of the C ABI: the library builds, loads and exports every
+function include/spotlight.h declares; host-side argument checking; the
+host delay table equals the oracle's bit for bit (Eq. 1)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2606_27262_gb300 as sp
+import synth
+from paper_2606_27262_gb300 import build as spbuild
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "spotlight.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    spbuild.build()
+    return sp.library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(sp.SIGNATURES), set(names) ^ set(sp.SIGNATURES)
+
+
+def test_strerror(lib):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -99):
+        assert isinstance(lib.sp_strerror(code), bytes)
+    assert lib.sp_strerror(-2).startswith(b"inconsistent")
+
+
+def test_workspace_sizes(lib):
+    assert lib.sp_sps_workspace_bytes(501, 8192, 6, 8192) == 2048 + 24064
+    assert lib.sp_sps_workspace_bytes(0, 10, 1, 0) == -1
+
+
+def test_argument_checks_need_no_gpu(lib):
+    f = synth.band_freqs(8)
+    d = np.array([0.0, 10.0])
+    h = ctypes.c_void_p()
+    bad_f = f[::-1].copy()  # increasing: the band must be flipped highest-first
+    assert lib.sp_plan_create(bad_f.ctypes.data, 8, 1e-3, d.ctypes.data, 2, ctypes.byref(h)) == sp.SP_EINVAL
+    neg = np.array([-1.0])
+    assert lib.sp_plan_create(f.ctypes.data, 8, 1e-3, neg.ctypes.data, 1, ctypes.byref(h)) == sp.SP_EINVAL
+    assert lib.sp_plan_create(f.ctypes.data, 8, 0.0, d.ctypes.data, 2, ctypes.byref(h)) == sp.SP_EINVAL
+    w = np.array([1, 2, 2], np.int32)  # not strictly increasing
+    assert lib.sp_single_pulse_search(1, 4, 100, w.ctypes.data, 3, 6.0, 0, 256, 1 << 20, 256, 10, 256, 0) \
+        == sp.SP_EINVAL
+    wbig = np.array([1, 2048], np.int32)
+    assert lib.sp_best_snr_map(1, 4, 100, wbig.ctypes.data, 2, 0, 256, 1 << 20, 256, 256, 0) == sp.SP_ELIMIT
+    w1 = np.array([1], np.int32)
+    assert lib.sp_single_pulse_search(1, 4, 100, w1.ctypes.data, 1, 6.0, 0, 256, 10, 256, 10, 256, 0) \
+        == sp.SP_EWORKSPACE
+
+
+@pytest.mark.parametrize("cfg", [synth.config1, synth.config2])
+def test_host_delays_equal_oracle(lib, cfg):
+    wl = cfg()
+    got, md = sp.compute_delays(wl.freqs, wl.tsamp, wl.dms)
+    want = oracle.delays(wl.freqs, wl.tsamp, wl.dms)
+    assert np.array_equal(got, want)
+    assert md == int(want.max())
+
+
+def test_host_delays_odd_plans(lib):
+    rng = np.random.default_rng(4)
+    for nchan in (1, 3, 100):
+        f = np.sort(rng.uniform(100, 1500, nchan))[::-1].copy()
+        if np.unique(f).size != nchan:
+            continue
+        dms = rng.uniform(0, 3000, 37)  # unsorted
+        got, md = sp.compute_delays(f, 6.4e-5, dms)
+        assert np.array_equal(got, oracle.delays(f, 6.4e-5, dms))

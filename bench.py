@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the SPOTLIGHT search hot path on GB300 (arXiv 2606.27262,
+Sec. 3.1): real-time beams per GPU for one full-size beam per step.
+
+Workload (one step = one beam through the whole path): 4096 channels over
+300-500 MHz, 1.31072 ms sampling, 131072 searched samples (+44995 overlap),
+5751 trial DMs on the 0.1/0.2/0.5/1.0 step schedule to 2000 pc cm^-3, boxcar
+widths 1..256, threshold 6 sigma, normalisation blocks of 8192 samples.  The
+input (721 MB) and the DM transform (3.0 GB) are larger than the 129 MB L2,
+so no L2 flush is needed between steps.
+
+  value   real-time beams = ranks * (131072 * 1.31072 ms) / device time per step
+          (transpose + dedispersion + block statistics + boxcar/peaks), inputs
+          resident in HBM.
+  e2e     the same metric through sp_searcher_run_host: pinned host input
+          copied in, candidates copied out, every step.
+  roofline  dedispersion kernel alone: channel x DM x sample adds per launch
+          over its CUDA-event time, against the integer-add issue rate
+          (SMs x measured 32-bit add lanes per SM per clock x max SM clock).
+
+`--impl reference` times the CPU oracle (test infrastructure) on a bounded
+sample of the same workload on the host cores.
+
+Multi-GPU (torchrun): every rank searches its own beam (replicas, weak
+scaling, no collective on the data path); the timed region is bracketed by
+barriers and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "real-time beams per GB300; dedispersion G(chan·DM·samp)/s vs roofline"
+MAX_SM_MHZ = 2070.0  # GB300 maximum SM clock
+KERNELS_PER_STEP = 4  # transpose, dedisperse, block statistics, boxcar/peaks
+PROFILE_JSON = os.path.join(ROOT, "profiles", "dedisperse_config2_traffic.json")
+DEDISP_SRC = os.path.join(ROOT, "paper_2606_27262_gb300", "csrc", "dedisperse.cu")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--cpu-stride", type=int, default=64,
+                   help="CPU baseline samples every n-th trial DM")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--n-out", type=int, default=None,
+                   help="searched samples per beam (default: the full 131072); smaller values are for "
+                        "profiler captures only")
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------ distributed --
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_init(world: int, backend: str):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x: float, world: int, device="cpu") -> float:
+    """Maximum of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def beam_seed(base: int, rank: int) -> int:
+    """Each rank searches a different synthetic beam."""
+    return base + 1000 * rank
+
+
+# ---------------------------------------------------------------- clocks --
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = sorted({name for r in rows for name, v in zip(self.REASONS, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------- workload --
+def workload(n_out=None):
+    import dataclasses
+
+    import synth
+    wl = synth.config2()
+    if n_out is not None and n_out != wl.n_out:
+        wl = dataclasses.replace(wl, n_out=int(n_out), name=wl.name.replace("131072", str(int(n_out))))
+    return wl
+
+
+def kernel_source_hash() -> str:
+    return hashlib.sha256(open(DEDISP_SRC, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(adds_per_launch: float):
+    """DRAM bytes per launch of the dedispersion kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    try:
+        prof = json.load(open(PROFILE_JSON))
+    except (OSError, ValueError):
+        return None
+    if prof.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return float(prof["dram_bytes_per_launch_full_config"])
+
+
+def cpu_oracle_sample(wl, plan_delays, x, stride: int):
+    """Time the oracle on every `stride`-th trial DM (full length, all
+    channels): dedispersion + best-width S/N.  Returns (seconds for the full
+    workload extrapolated by trial count, sample description, threads)."""
+    import numpy as np
+
+    import oracle
+    rows = np.arange(0, plan_delays.shape[0], stride)
+    t = time.perf_counter()
+    dmt = oracle.dedisperse(x, plan_delays[rows], wl.n_out)
+    oracle.best(dmt, wl.widths, wl.norm_block)
+    dt = time.perf_counter() - t
+    full = dt * plan_delays.shape[0] / rows.size
+    desc = (f"oracle dedispersion + boxcar S/N on every {stride}th trial DM ({rows.size} of "
+            f"{plan_delays.shape[0]}) x {wl.n_out} samples x {wl.nchan} ch, {dt:.1f} s, "
+            f"scaled by trial count")
+    return full, desc, oracle.num_threads()
+
+
+def config_dict(wl, plan_ndm, max_delay):
+    return {
+        "workload": wl.name,
+        "nchan": wl.nchan, "n_out": wl.n_out, "n_in": wl.n_out + max_delay, "ndm": plan_ndm,
+        "widths": [int(w) for w in wl.widths], "threshold": wl.threshold, "norm_block": wl.norm_block,
+        "tsamp_s": wl.tsamp, "l2": "inputs larger than L2 (721 MB filterbank, 3.0 GB DM transform), no flush",
+    }
+
+
+# ------------------------------------------------------------------ ours --
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2606_27262_gb300 as sp
+    import synth
+    from paper_2606_27262_gb300 import build as spbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    spbuild.build()
+    wl = workload(args.n_out)
+    plan = sp.Plan(wl.freqs, wl.tsamp, wl.dms)
+    n_in = wl.n_out + plan.max_delay
+    x, _ = synth.make_workload_beam(wl, n_in, seed=beam_seed(wl.seed, rank))
+
+    d_in = torch.from_numpy(x).to(dev)
+    pitch = sp.cm_pitch(n_in)
+    xt = torch.empty((wl.nchan, pitch), dtype=torch.uint8, device=dev)
+    dmt = torch.empty((plan.ndm, wl.n_out), dtype=torch.int32, device=dev)
+    sw = torch.empty(sp.sps_workspace_bytes(plan.ndm, wl.n_out, len(wl.widths), wl.norm_block),
+                     dtype=torch.uint8, device=dev)
+    cap = 1 << 22
+    cands = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        sp.transpose_to_cm(d_in, xt, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        sp.dedisperse_cm(plan, xt, n_in, dmt, stream)
+        if ev is not None:
+            ev[2].record(stream)
+        sp.single_pulse_search(dmt, wl.widths, wl.threshold, wl.norm_block, sw, cands, cnt, stream)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    lanes, nsm = sp.probe_iadd3_rate()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    elapsed = reduce_max(t_start.elapsed_time(t_end), world, dev)
+    ms_step = elapsed / args.steps
+    tr_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    dd_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    sps_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    ncand = int(cnt.item())
+    beam_s = wl.n_out * wl.tsamp
+    value = world * beam_s / (ms_step / 1e3)
+    adds = float(wl.nchan) * plan.ndm * wl.n_out
+    achieved = adds / (dd_ms / 1e3) / 1e12
+    peak = nsm * lanes * MAX_SM_MHZ * 1e6 / 1e12
+
+    e2e = None
+    if not args.no_e2e:
+        del xt
+        s = sp.Searcher(plan, wl.n_out, wl.widths, wl.threshold, wl.norm_block, cap)
+        h_in = torch.from_numpy(x).pin_memory()
+        hc = np.empty((cap, 4), np.int32)
+        s.run_host(h_in, hc)
+        barrier(world)
+        t0 = time.perf_counter()
+        n_found = 0
+        for _ in range(args.steps):
+            n_found = s.run_host(h_in, hc)
+        e2e_s = reduce_max(time.perf_counter() - t0, world, dev) / args.steps
+        barrier(world)
+        e2e = {"value": world * beam_s / e2e_s, "unit": "beams", "ms_per_step": e2e_s * 1e3,
+               "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": 8 + 16 * min(n_found, cap),
+               "api": "sp_searcher_run_host"}
+        s.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        full_s, desc, cores = cpu_oracle_sample(wl, plan.delays(), x, args.cpu_stride)
+        cpu = {"value": beam_s / full_s, "unit": "beams", "cores": cores, "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "beams", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded noise + injected dispersed bursts)",
+        "config": config_dict(wl, plan.ndm, plan.max_delay) | {"parallelism": f"replicas x{world}"},
+        "gchan_dm_samp_per_s": adds / (ms_step / 1e3) / 1e9,
+        "stage_ms": {"transpose": tr_ms, "dedisperse": dd_ms, "single_pulse_search": sps_ms},
+        "candidates_per_beam": ncand,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(adds),
+                     "kernel": "dedisperse_kernel",
+                     "peak_basis": f"{nsm} SMs x {lanes:.1f} measured 32-bit add lanes/SM/clk x "
+                                   f"{MAX_SM_MHZ:.0f} MHz"},
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": KERNELS_PER_STEP * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- reference --
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+
+    import oracle
+    import synth
+    wl = workload(args.n_out)
+    delays = oracle.delays(wl.freqs, wl.tsamp, wl.dms)
+    n_in = wl.n_out + int(delays.max())
+    x, _ = synth.make_workload_beam(wl, n_in)
+    beam_s = wl.n_out * wl.tsamp
+    for _ in range(max(args.warmup, 0)):
+        cpu_oracle_sample(wl, delays, x, args.cpu_stride * 4)
+    times, desc, cores = [], "", oracle.num_threads()
+    for _ in range(args.steps):
+        full_s, desc, cores = cpu_oracle_sample(wl, delays, x, args.cpu_stride)
+        times.append(full_s)
+    ms_step = statistics.mean(times) * 1e3
+    value = beam_s / (ms_step / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "beams", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": config_dict(wl, delays.shape[0], int(delays.max())) | {"parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "beams", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "beams", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -111,6 +111,23 @@ int sp_dedisperse(const sp_plan *plan, const uint8_t *d_in, int64_t n_in,
                   int32_t *d_out, int64_t n_out, void *d_work, int64_t work_bytes,
                   void *stream);
 
+/* The two steps of sp_dedisperse, for callers whose input already sits in
+ * channel-major order (for example a ring buffer kept per channel).
+ * sp_cm_pitch(n_in): the smallest row pitch (bytes) a channel-major input of
+ * n_in samples needs: the kernel reads up to that many bytes of each row;
+ * bytes at and past n_in only reach outputs t >= n_out, which are not
+ * written, so their contents do not matter.
+ * sp_transpose_to_cm: d_in [n_in][nchan] (time-major, 16-byte aligned) ->
+ *   d_xt [nchan][pitch] (pitch >= sp_cm_pitch(n_in), multiple of 64; bytes
+ *   past n_in are zeroed).
+ * sp_dedisperse_cm: the DM transform of d_xt [nchan][pitch] (256-byte
+ *   aligned), same definition and shape rule as sp_dedisperse. */
+int64_t sp_cm_pitch(int64_t n_in);
+int sp_transpose_to_cm(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_xt,
+                       int64_t pitch, void *stream);
+int sp_dedisperse_cm(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, int64_t n_in,
+                     int32_t *d_out, int64_t n_out, void *stream);
+
 /* ------------------------------------------------- single-pulse search --
  * Boxcar matched-filter search of a DM transform (Sec. 3.1.2).
  * Normalisation: each row is cut into nblk = max(1, n_out / norm_block)

@@ -51,6 +51,9 @@ SIGNATURES = {
     "sp_compute_delays": (ctypes.c_int, [P, I32, F64, P, I32, P, P]),
     "sp_dedisperse_workspace_bytes": (I64, [P, I64]),
     "sp_dedisperse": (ctypes.c_int, [P, P, I64, P, I64, P, I64, P]),
+    "sp_cm_pitch": (I64, [I64]),
+    "sp_transpose_to_cm": (ctypes.c_int, [P, I64, I32, P, I64, P]),
+    "sp_dedisperse_cm": (ctypes.c_int, [P, P, I64, I64, P, I64, P]),
     "sp_sps_workspace_bytes": (I64, [I32, I64, I32, I64]),
     "sp_single_pulse_search": (ctypes.c_int, [P, I32, I64, P, I32, F32, I64, P, I64, P, I64, P, P]),
     "sp_best_snr_map": (ctypes.c_int, [P, I32, I64, P, I32, I64, P, I64, P, P, P]),
@@ -58,6 +61,7 @@ SIGNATURES = {
     "sp_searcher_destroy": (ctypes.c_int, [P]),
     "sp_searcher_run": (ctypes.c_int, [P, P, P, I64, P, P]),
     "sp_searcher_run_host": (ctypes.c_int, [P, P, P, I64, P, P]),
+    "sp_probe_iadd3_rate": (ctypes.c_int, [ctypes.c_int, P, P]),
 }
 
 
@@ -171,6 +175,22 @@ def dedisperse(plan: Plan, d_in, d_out, d_work, stream=None):
                                 int(d_work.numel()), _stream(stream)), "sp_dedisperse")
 
 
+def cm_pitch(n_in: int) -> int:
+    return int(_lib().sp_cm_pitch(int(n_in)))
+
+
+def transpose_to_cm(d_in, d_xt, stream=None):
+    """d_in uint8 [n_in][nchan] -> d_xt uint8 [nchan][pitch] (channel-major)."""
+    _check(_lib().sp_transpose_to_cm(_ptr(d_in), int(d_in.shape[0]), int(d_in.shape[1]), _ptr(d_xt),
+                                     int(d_xt.shape[1]), _stream(stream)), "sp_transpose_to_cm")
+
+
+def dedisperse_cm(plan: Plan, d_xt, n_in: int, d_out, stream=None):
+    """DM transform of a channel-major input d_xt uint8 [nchan][pitch]."""
+    _check(_lib().sp_dedisperse_cm(plan.handle, _ptr(d_xt), int(d_xt.shape[1]), int(n_in), _ptr(d_out),
+                                   int(d_out.shape[1]), _stream(stream)), "sp_dedisperse_cm")
+
+
 def single_pulse_search(d_dmt, widths, threshold: float, norm_block: int, d_work, d_cands, d_count,
                         stream=None):
     """d_dmt: int32 [ndm][n_out]; d_cands: int32 [cap][4] CUDA tensor (sp_cand
@@ -236,3 +256,12 @@ class Searcher:
             self.close()
         except Exception:
             pass
+
+
+def probe_iadd3_rate(iters: int = 4096):
+    """(3-input integer adds per SM per clock, SM count) measured on the
+    current device (include/spotlight_probe.h)."""
+    r = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(_lib().sp_probe_iadd3_rate(int(iters), ctypes.byref(r), ctypes.byref(n)), "sp_probe_iadd3_rate")
+    return float(r.value), int(n.value)

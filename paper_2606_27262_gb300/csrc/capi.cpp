@@ -89,6 +89,28 @@ extern "C" int sp_dedisperse(const sp_plan *p, const uint8_t *d_in, int64_t n_in
     return launch_dedisperse(p, xt, pitch, n_out, d_out, s);
 }
 
+extern "C" int64_t sp_cm_pitch(int64_t n_in) { return n_in > 0 ? dedisp_pitch(n_in) : -1; }
+
+extern "C" int sp_transpose_to_cm(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_xt, int64_t pitch,
+                                  void *stream) {
+    if (!d_in || !d_xt || n_in <= 0 || nchan <= 0) return SP_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_in) & 15) || (reinterpret_cast<uintptr_t>(d_xt) & 15)) return SP_EINVAL;
+    if (pitch < dedisp_pitch(n_in) || (pitch & 63)) return SP_EINVAL;
+    if (n_in > (int64_t)INT32_MAX - 4096 || (nchan + 63) / 64 > 65535) return SP_ELIMIT;
+    return launch_transpose(d_in, n_in, nchan, d_xt, pitch, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int sp_dedisperse_cm(const sp_plan *p, const uint8_t *d_xt, int64_t pitch, int64_t n_in, int32_t *d_out,
+                                int64_t n_out, void *stream) {
+    if (!p || !d_xt || !d_out || n_in <= 0 || n_out <= 0) return SP_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_xt) & 255) || pitch < dedisp_pitch(n_in) || (pitch & 15)) return SP_EINVAL;
+    if (!on_plan_device(p)) return SP_EINVAL;
+    if (n_out != n_in - p->max_delay) return SP_ESHAPE;
+    if (n_in > (int64_t)INT32_MAX - 4096 || (n_out + kDedispTimeTile - 1) / kDedispTimeTile > 65535)
+        return SP_ELIMIT;
+    return launch_dedisperse(p, d_xt, pitch, n_out, d_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
 extern "C" int64_t sp_sps_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block) {
     if (ndm <= 0 || n_out <= 0 || nw <= 0) return -1;
     return sps_workspace_bytes(ndm, n_out, nw, norm_block);

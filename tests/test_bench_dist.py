@@ -1,0 +1,65 @@
+"""bench.py's multi-rank helpers on CPU with the gloo backend (world size 2):
+the slowest rank's time wins, every rank searches its own beam, and the
+JSON-line helpers need no GPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    r, w, lr = bench.dist_env()
+    bench.dist_init(w, "gloo")
+    bench.barrier(w)
+    m = bench.reduce_max(10.0 * (r + 1), w)
+    seed = bench.beam_seed(1002, r)
+    q.put((r, m, seed))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_two_rank_max_and_distinct_beams():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [m for _, m, _ in res] == [20.0, 20.0]
+    assert len({s for _, _, s in res}) == world
+
+
+def test_single_rank_helpers():
+    assert bench.reduce_max(3.5, 1) == 3.5
+    bench.barrier(1)
+    wl = bench.workload(4096)
+    assert wl.n_out == 4096 and wl.nchan == 4096
+    assert bench.workload().n_out == 131072
+
+
+def test_profiled_traffic_guard(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "PROFILE_JSON", str(tmp_path / "p.json"))
+    assert bench.profiled_traffic(1.0) is None
+    (tmp_path / "p.json").write_text('{"kernel_source_sha256_16": "stale", "dram_bytes_per_launch_full_config": 5}')
+    assert bench.profiled_traffic(1.0) is None
+    h = bench.kernel_source_hash()
+    (tmp_path / "p.json").write_text('{"kernel_source_sha256_16": "%s", "dram_bytes_per_launch_full_config": 5}' % h)
+    assert bench.profiled_traffic(1.0) == 5.0

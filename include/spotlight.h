@@ -161,6 +161,30 @@ int sp_single_pulse_search(const int32_t *d_dmt, int32_t ndm, int64_t n_out,
                            int64_t norm_block, void *d_work, int64_t work_bytes,
                            sp_cand *d_cands, int64_t cap, int64_t *d_count,
                            void *stream);
+/* Allocation-free variant of sp_single_pulse_search.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * when they search -- a real-time loop that claimed its whole memory budget
+ * at start-up and must not block or fail on an allocation mid-stream, a host
+ * whose device memory belongs entirely to its own pool allocator, a plug-in
+ * that is not permitted to call cudaMalloc.  Same arguments, arithmetic,
+ * outputs and errors as sp_single_pulse_search, minus the workspace: the
+ * block statistics live in a library-owned device array of
+ * SP_NOALLOC_SCRATCH_BYTES (16 MiB), present on every GPU that loads the
+ * library until the process exits.  Requests whose statistics need more
+ * (sp_sps_workspace_bytes(ndm, n_out, nw, norm_block) > 16 MiB; config 2,
+ * 5751 DMs x 131072 samples / 8192-sample blocks x 9 widths, needs 6.9 MB)
+ * return SP_ELIMIT.  The call allocates nothing: no cudaMalloc, no cudaFree.
+ * The first call on a device looks up the array's device address with that
+ * device current (make that first call before any stream capture).  Every
+ * call on a device shares the one array and it keeps the last call's
+ * contents (each call overwrites what it reads); calls whose GPU work
+ * overlaps -- on different streams or different host threads -- race on it
+ * and must be serialised by the caller. */
+#define SP_NOALLOC_SCRATCH_BYTES (16 << 20)
+int sp_single_pulse_search_noalloc(const int32_t *d_dmt, int32_t ndm, int64_t n_out,
+                                   const int32_t *h_widths, int32_t nw, float threshold,
+                                   int64_t norm_block, sp_cand *d_cands, int64_t cap,
+                                   int64_t *d_count, void *stream);
 /* The map the candidates are picked from: d_best [ndm][n_out] float (best
  * S/N, -inf where no width fits) and d_wbest [ndm][n_out] int8 (index of the
  * best width, -1 where none fits).  Same arguments and arithmetic as

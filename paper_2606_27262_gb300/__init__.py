@@ -56,6 +56,7 @@ SIGNATURES = {
     "sp_dedisperse_cm": (ctypes.c_int, [P, P, I64, I64, P, I64, P]),
     "sp_sps_workspace_bytes": (I64, [I32, I64, I32, I64]),
     "sp_single_pulse_search": (ctypes.c_int, [P, I32, I64, P, I32, F32, I64, P, I64, P, I64, P, P]),
+    "sp_single_pulse_search_noalloc": (ctypes.c_int, [P, I32, I64, P, I32, F32, I64, P, I64, P, P]),
     "sp_best_snr_map": (ctypes.c_int, [P, I32, I64, P, I32, I64, P, I64, P, P, P]),
     "sp_searcher_create": (ctypes.c_int, [P, I64, P, I32, F32, I64, I64, P]),
     "sp_searcher_destroy": (ctypes.c_int, [P]),
@@ -200,6 +201,24 @@ def single_pulse_search(d_dmt, widths, threshold: float, norm_block: int, d_work
                                          w.size, float(threshold), int(norm_block), _ptr(d_work),
                                          int(d_work.numel()), _ptr(d_cands), int(d_cands.shape[0]),
                                          _ptr(d_count), _stream(stream)), "sp_single_pulse_search")
+
+
+SP_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def single_pulse_search_noalloc(d_dmt, widths, threshold: float, norm_block: int, d_cands, d_count,
+                                stream=None):
+    """sp_single_pulse_search without a workspace: for callers that cannot
+    allocate device memory while searching (a real-time loop with its memory
+    budget fixed at start-up, a host whose device memory belongs to its own
+    pool, a plug-in barred from cudaMalloc).  The block statistics live in a
+    16 MiB library-owned device array shared by every call on the device, so
+    calls whose GPU work overlaps must be serialised by the caller."""
+    w = _widths(widths)
+    _check(_lib().sp_single_pulse_search_noalloc(_ptr(d_dmt), int(d_dmt.shape[0]), int(d_dmt.shape[1]),
+                                                 w.ctypes.data, w.size, float(threshold), int(norm_block),
+                                                 _ptr(d_cands), int(d_cands.shape[0]), _ptr(d_count),
+                                                 _stream(stream)), "sp_single_pulse_search_noalloc")
 
 
 def best_snr_map(d_dmt, widths, norm_block: int, d_work, d_best, d_wbest, stream=None):

@@ -10,7 +10,7 @@ input (721 MB) and the DM transform (3.0 GB) are larger than the 129 MB L2,
 so no L2 flush is needed between steps.
 
   value   real-time beams = ranks * (131072 * 1.31072 ms) / device time per step
-          (transpose + dedispersion + block statistics + boxcar/peaks), inputs
+          (input staging + dedispersion + block statistics + boxcar/peaks), inputs
           resident in HBM.
   e2e     the same metric through sp_searcher_run_host: pinned host input
           copied in, candidates copied out, every step.
@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "real-time beams per GB300; dedispersion G(chan·DM·samp)/s vs roofline"
 MAX_SM_MHZ = 2070.0  # GB300 maximum SM clock
-KERNELS_PER_STEP = 4  # transpose, dedisperse, block statistics, boxcar/peaks
+KERNELS_PER_STEP = 4  # input staging, dedisperse, block statistics, boxcar/peaks
 PROFILE_JSON = os.path.join(ROOT, "profiles", "dedisperse_config2_traffic.json")
 DEDISP_SRC = os.path.join(ROOT, "paper_2606_27262_gb300", "csrc", "dedisperse.cu")
 
@@ -220,8 +220,7 @@ def run_ours(args):
     x, _ = synth.make_workload_beam(wl, n_in, seed=beam_seed(wl.seed, rank))
 
     d_in = torch.from_numpy(x).to(dev)
-    pitch = sp.cm_pitch(n_in)
-    xt = torch.empty((wl.nchan, pitch), dtype=torch.uint8, device=dev)
+    xt = sp.staged_buffer(wl.nchan, n_in, dev)
     dmt = torch.empty((plan.ndm, wl.n_out), dtype=torch.int32, device=dev)
     sw = torch.empty(sp.sps_workspace_bytes(plan.ndm, wl.n_out, len(wl.widths), wl.norm_block),
                      dtype=torch.uint8, device=dev)
@@ -233,10 +232,10 @@ def run_ours(args):
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        sp.transpose_to_cm(d_in, xt, stream)
+        sp.stage_input(d_in, xt, stream)
         if ev is not None:
             ev[1].record(stream)
-        sp.dedisperse_cm(plan, xt, n_in, dmt, stream)
+        sp.dedisperse_staged(plan, xt, n_in, dmt, stream)
         if ev is not None:
             ev[2].record(stream)
         sp.single_pulse_search(dmt, wl.widths, wl.threshold, wl.norm_block, sw, cands, cnt, stream)
@@ -303,7 +302,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded noise + injected dispersed bursts)",
         "config": config_dict(wl, plan.ndm, plan.max_delay) | {"parallelism": f"replicas x{world}"},
         "gchan_dm_samp_per_s": adds / (ms_step / 1e3) / 1e9,
-        "stage_ms": {"transpose": tr_ms, "dedisperse": dd_ms, "single_pulse_search": sps_ms},
+        "stage_ms": {"stage_input": tr_ms, "dedisperse": dd_ms, "single_pulse_search": sps_ms},
         "candidates_per_beam": ncand,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(adds),

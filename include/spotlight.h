@@ -84,6 +84,11 @@ int sp_plan_destroy(sp_plan *plan);
 /* max_delay = the largest delay[d][c] (D_max, samples); any out pointer may
  * be NULL. */
 int sp_plan_info(const sp_plan *plan, int32_t *max_delay, int32_t *nchan, int32_t *ndm);
+/* Device status word of the plan's kernels: 0, or SP_STATUS_* bits set by
+ * a kernel that gave up a bounded wait (its outputs are then invalid).
+ * Reads it after synchronising the device; clear != 0 resets it. */
+#define SP_STATUS_STAGING_TIMEOUT 1
+int sp_plan_status(const sp_plan *plan, int32_t *h_status, int32_t clear);
 /* Copies the delay table, int32 [ndm][nchan], to host memory. */
 int sp_plan_delays(const sp_plan *plan, int32_t *h_out);
 /* The same delay table computed on the host only (no device, no plan):
@@ -103,30 +108,30 @@ int sp_compute_delays(const double *freqs_mhz, int32_t nchan, double tsamp_s,
  *   d_out [ndm][n_out]  int32, device.
  *   d_work / work_bytes: device scratch of at least
  *         sp_dedisperse_workspace_bytes(plan, n_in) bytes, 256-byte aligned
- *         (holds a channel-major copy of the input); contents on entry are
- *         ignored, on return undefined.
+ *         (holds the staged input, see sp_stage_input); contents on entry
+ *         are ignored, on return they hold the staged input.
  * Errors: SP_EINVAL, SP_ESHAPE, SP_EWORKSPACE, SP_ELIMIT, SP_ECUDA (launch). */
 int64_t sp_dedisperse_workspace_bytes(const sp_plan *plan, int64_t n_in);
 int sp_dedisperse(const sp_plan *plan, const uint8_t *d_in, int64_t n_in,
                   int32_t *d_out, int64_t n_out, void *d_work, int64_t work_bytes,
                   void *stream);
 
-/* The two steps of sp_dedisperse, for callers whose input already sits in
- * channel-major order (for example a ring buffer kept per channel).
- * sp_cm_pitch(n_in): the smallest row pitch (bytes) a channel-major input of
- * n_in samples needs: the kernel reads up to that many bytes of each row;
- * bytes at and past n_in only reach outputs t >= n_out, which are not
- * written, so their contents do not matter.
- * sp_transpose_to_cm: d_in [n_in][nchan] (time-major, 16-byte aligned) ->
- *   d_xt [nchan][pitch] (pitch >= sp_cm_pitch(n_in), multiple of 64; bytes
- *   past n_in are zeroed).
- * sp_dedisperse_cm: the DM transform of d_xt [nchan][pitch] (256-byte
- *   aligned), same definition and shape rule as sp_dedisperse. */
-int64_t sp_cm_pitch(int64_t n_in);
-int sp_transpose_to_cm(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_xt,
-                       int64_t pitch, void *stream);
-int sp_dedisperse_cm(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, int64_t n_in,
-                     int32_t *d_out, int64_t n_out, void *stream);
+/* The two steps of sp_dedisperse, for callers that stage an input once and
+ * search it several times, or keep it staged in a ring buffer.
+ * The staged form is the input rearranged for the dedispersion kernel; its
+ * layout belongs to the library (currently channel-major uint8
+ * [nchan][pitch], zero at and past n_in) and is produced by sp_stage_input.
+ * It takes sp_staged_bytes(nchan, n_in) bytes, 256-byte aligned, with row
+ * pitch sp_staged_pitch(n_in).
+ * sp_stage_input: d_in [n_in][nchan] (time-major, 16-byte aligned) ->
+ *   d_staged.  sp_dedisperse_staged: the DM transform of d_staged, same
+ *   definition, shape rule and errors as sp_dedisperse. */
+int64_t sp_staged_pitch(int64_t n_in);
+int64_t sp_staged_bytes(int32_t nchan, int64_t n_in);
+int sp_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_staged,
+                   int64_t pitch, void *stream);
+int sp_dedisperse_staged(const sp_plan *plan, const uint8_t *d_staged, int64_t pitch, int64_t n_in,
+                         int32_t *d_out, int64_t n_out, void *stream);
 
 /* ------------------------------------------------- single-pulse search --
  * Boxcar matched-filter search of a DM transform (Sec. 3.1.2).

@@ -48,12 +48,14 @@ SIGNATURES = {
     "sp_plan_destroy": (ctypes.c_int, [P]),
     "sp_plan_info": (ctypes.c_int, [P, P, P, P]),
     "sp_plan_delays": (ctypes.c_int, [P, P]),
+    "sp_plan_status": (ctypes.c_int, [P, P, I32]),
     "sp_compute_delays": (ctypes.c_int, [P, I32, F64, P, I32, P, P]),
     "sp_dedisperse_workspace_bytes": (I64, [P, I64]),
     "sp_dedisperse": (ctypes.c_int, [P, P, I64, P, I64, P, I64, P]),
-    "sp_cm_pitch": (I64, [I64]),
-    "sp_transpose_to_cm": (ctypes.c_int, [P, I64, I32, P, I64, P]),
-    "sp_dedisperse_cm": (ctypes.c_int, [P, P, I64, I64, P, I64, P]),
+    "sp_staged_pitch": (I64, [I64]),
+    "sp_staged_bytes": (I64, [I32, I64]),
+    "sp_stage_input": (ctypes.c_int, [P, I64, I32, P, I64, P]),
+    "sp_dedisperse_staged": (ctypes.c_int, [P, P, I64, I64, P, I64, P]),
     "sp_sps_workspace_bytes": (I64, [I32, I64, I32, I64]),
     "sp_single_pulse_search": (ctypes.c_int, [P, I32, I64, P, I32, F32, I64, P, I64, P, I64, P, P]),
     "sp_single_pulse_search_noalloc": (ctypes.c_int, [P, I32, I64, P, I32, F32, I64, P, I64, P, P]),
@@ -137,6 +139,12 @@ class Plan:
         _check(_lib().sp_plan_delays(self._h, out.ctypes.data), "sp_plan_delays")
         return out
 
+    def status(self, clear: bool = False) -> int:
+        """Device status word (0 = ok; SP_STATUS_* bits otherwise)."""
+        v = ctypes.c_int32()
+        _check(_lib().sp_plan_status(self._h, ctypes.byref(v), int(clear)), "sp_plan_status")
+        return int(v.value)
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib().sp_plan_destroy(self._h)
@@ -176,20 +184,30 @@ def dedisperse(plan: Plan, d_in, d_out, d_work, stream=None):
                                 int(d_work.numel()), _stream(stream)), "sp_dedisperse")
 
 
-def cm_pitch(n_in: int) -> int:
-    return int(_lib().sp_cm_pitch(int(n_in)))
+def staged_pitch(n_in: int) -> int:
+    return int(_lib().sp_staged_pitch(int(n_in)))
 
 
-def transpose_to_cm(d_in, d_xt, stream=None):
-    """d_in uint8 [n_in][nchan] -> d_xt uint8 [nchan][pitch] (channel-major)."""
-    _check(_lib().sp_transpose_to_cm(_ptr(d_in), int(d_in.shape[0]), int(d_in.shape[1]), _ptr(d_xt),
-                                     int(d_xt.shape[1]), _stream(stream)), "sp_transpose_to_cm")
+def staged_bytes(nchan: int, n_in: int) -> int:
+    return int(_lib().sp_staged_bytes(int(nchan), int(n_in)))
 
 
-def dedisperse_cm(plan: Plan, d_xt, n_in: int, d_out, stream=None):
-    """DM transform of a channel-major input d_xt uint8 [nchan][pitch]."""
-    _check(_lib().sp_dedisperse_cm(plan.handle, _ptr(d_xt), int(d_xt.shape[1]), int(n_in), _ptr(d_out),
-                                   int(d_out.shape[1]), _stream(stream)), "sp_dedisperse_cm")
+def staged_buffer(nchan: int, n_in: int, device="cuda"):
+    """A device buffer for the staged form of an input (sp_stage_input)."""
+    import torch
+    return torch.empty(staged_bytes(nchan, n_in), dtype=torch.uint8, device=device)
+
+
+def stage_input(d_in, d_staged, stream=None):
+    """d_in uint8 [n_in][nchan] -> d_staged (staged_buffer(nchan, n_in))."""
+    _check(_lib().sp_stage_input(_ptr(d_in), int(d_in.shape[0]), int(d_in.shape[1]), _ptr(d_staged),
+                                 staged_pitch(int(d_in.shape[0])), _stream(stream)), "sp_stage_input")
+
+
+def dedisperse_staged(plan: Plan, d_staged, n_in: int, d_out, stream=None):
+    """DM transform of a staged input (staged_buffer(nchan, n_in))."""
+    _check(_lib().sp_dedisperse_staged(plan.handle, _ptr(d_staged), staged_pitch(int(n_in)), int(n_in), _ptr(d_out),
+                                       int(d_out.shape[1]), _stream(stream)), "sp_dedisperse_staged")
 
 
 def single_pulse_search(d_dmt, widths, threshold: float, norm_block: int, d_work, d_cands, d_count,

@@ -66,49 +66,59 @@ extern "C" const char *sp_strerror(int code) {
     }
 }
 
+extern "C" int64_t sp_staged_pitch(int64_t n_in) { return n_in > 0 ? dedisp_pitch(n_in) : -1; }
+
+extern "C" int64_t sp_staged_bytes(int32_t nchan, int64_t n_in) {
+    if (nchan <= 0 || n_in <= 0) return -1;
+    return align256((int64_t)nchan * dedisp_pitch(n_in));
+}
+
 extern "C" int64_t sp_dedisperse_workspace_bytes(const sp_plan *p, int64_t n_in) {
     if (!p || n_in <= 0) return -1;
-    return align256((int64_t)p->nchan * dedisp_pitch(n_in));
+    return sp_staged_bytes(p->nchan, n_in);
+}
+
+static int check_dedisp_shape(const sp_plan *p, int64_t n_in, int64_t n_out) {
+    if (!on_plan_device(p)) return SP_EINVAL;
+    if (n_out != n_in - p->max_delay) return SP_ESHAPE;
+    if (n_in > (int64_t)INT32_MAX - 4096 || (n_out + kDedispTimeTile - 1) / kDedispTimeTile > 65535)
+        return SP_ELIMIT;
+    return SP_OK;
 }
 
 extern "C" int sp_dedisperse(const sp_plan *p, const uint8_t *d_in, int64_t n_in, int32_t *d_out, int64_t n_out,
                              void *d_work, int64_t work_bytes, void *stream) {
     if (!p || !d_in || !d_out || n_in <= 0 || n_out <= 0) return SP_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_in) & 15) return SP_EINVAL;
-    if (!on_plan_device(p)) return SP_EINVAL;
-    if (n_out != n_in - p->max_delay) return SP_ESHAPE;
-    if (n_in > (int64_t)INT32_MAX - 4096 || (n_out + kDedispTimeTile - 1) / kDedispTimeTile > 65535)
-        return SP_ELIMIT;
+    int rc = check_dedisp_shape(p, n_in, n_out);
+    if (rc) return rc;
     const int64_t pitch = dedisp_pitch(n_in);
-    if (!d_work || work_bytes < (int64_t)p->nchan * pitch || (reinterpret_cast<uintptr_t>(d_work) & 255))
+    if (!d_work || work_bytes < sp_staged_bytes(p->nchan, n_in) || (reinterpret_cast<uintptr_t>(d_work) & 255))
         return SP_EWORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    uint8_t *xt = reinterpret_cast<uint8_t *>(d_work);
-    int rc = launch_transpose(d_in, n_in, p->nchan, xt, pitch, s);
+    uint8_t *staged = reinterpret_cast<uint8_t *>(d_work);
+    rc = launch_stage_input(d_in, n_in, p->nchan, staged, pitch, s);
     if (rc) return rc;
-    return launch_dedisperse(p, xt, pitch, n_out, d_out, s);
+    return launch_dedisperse(p, staged, pitch, n_out, d_out, s);
 }
 
-extern "C" int64_t sp_cm_pitch(int64_t n_in) { return n_in > 0 ? dedisp_pitch(n_in) : -1; }
-
-extern "C" int sp_transpose_to_cm(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_xt, int64_t pitch,
-                                  void *stream) {
-    if (!d_in || !d_xt || n_in <= 0 || nchan <= 0) return SP_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(d_in) & 15) || (reinterpret_cast<uintptr_t>(d_xt) & 15)) return SP_EINVAL;
+extern "C" int sp_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_staged, int64_t pitch,
+                              void *stream) {
+    if (!d_in || !d_staged || n_in <= 0 || nchan <= 0) return SP_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_in) & 15) || (reinterpret_cast<uintptr_t>(d_staged) & 255)) return SP_EINVAL;
     if (pitch < dedisp_pitch(n_in) || (pitch & 63)) return SP_EINVAL;
     if (n_in > (int64_t)INT32_MAX - 4096 || (nchan + 63) / 64 > 65535) return SP_ELIMIT;
-    return launch_transpose(d_in, n_in, nchan, d_xt, pitch, reinterpret_cast<cudaStream_t>(stream));
+    return launch_stage_input(d_in, n_in, nchan, d_staged, pitch, reinterpret_cast<cudaStream_t>(stream));
 }
 
-extern "C" int sp_dedisperse_cm(const sp_plan *p, const uint8_t *d_xt, int64_t pitch, int64_t n_in, int32_t *d_out,
-                                int64_t n_out, void *stream) {
-    if (!p || !d_xt || !d_out || n_in <= 0 || n_out <= 0) return SP_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(d_xt) & 255) || pitch < dedisp_pitch(n_in) || (pitch & 15)) return SP_EINVAL;
-    if (!on_plan_device(p)) return SP_EINVAL;
-    if (n_out != n_in - p->max_delay) return SP_ESHAPE;
-    if (n_in > (int64_t)INT32_MAX - 4096 || (n_out + kDedispTimeTile - 1) / kDedispTimeTile > 65535)
-        return SP_ELIMIT;
-    return launch_dedisperse(p, d_xt, pitch, n_out, d_out, reinterpret_cast<cudaStream_t>(stream));
+extern "C" int sp_dedisperse_staged(const sp_plan *p, const uint8_t *d_staged, int64_t pitch, int64_t n_in,
+                                    int32_t *d_out, int64_t n_out, void *stream) {
+    if (!p || !d_staged || !d_out || n_in <= 0 || n_out <= 0) return SP_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_staged) & 255) || pitch < dedisp_pitch(n_in) || (pitch & 63))
+        return SP_EINVAL;
+    const int rc = check_dedisp_shape(p, n_in, n_out);
+    if (rc) return rc;
+    return launch_dedisperse(p, d_staged, pitch, n_out, d_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int64_t sp_sps_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block) {

@@ -5,45 +5,43 @@
 //   out[d][t] = sum_c in[t + delay[d][c]][c]
 //
 // Two kernels:
-//   transpose_u8_kernel  time-major [n_in][nchan] -> channel-major
-//                        [nchan][pitch] (zero padded), so that one channel's
-//                        time series is contiguous.
-//   dedisperse_kernel    one CTA = 32 consecutive trial DMs (a "DM tile" from
-//                        the plan) x 512 output samples.  For each chunk of
-//                        16 channels it stages, per channel, the window of
-//                        input samples that the tile's 32 delays reach
-//                        (512 + delay spread + alignment slack) into shared
-//                        memory as four copies shifted by 0..3 bytes, so that
-//                        any 4 consecutive samples are one aligned 32-bit
-//                        load.  One staged byte then serves up to 32 DMs.
+//   stage_input_kernel  time-major [n_in][nchan] -> channel-major
+//                       [nchan][pitch] (zero padded), so that one channel's
+//                       time series is contiguous.
+//   dedisperse_kernel   one CTA = up to 32 consecutive trial DMs (a "DM tile"
+//                       from the plan) x 512 output samples.  Channels go in
+//                       chunks of 8: per channel the CTA stages the window of
+//                       input samples the tile's delays reach (512 + delay
+//                       spread + alignment slack).  Warp 0 fetches chunk k+1
+//                       with bulk asynchronous copies (TMA) while the CTA
+//                       sums chunk k; each warp then expands one channel of
+//                       the fetched chunk into four copies shifted by 0..3
+//                       bytes, so that any 4 consecutive samples are one
+//                       aligned 32-bit load.  One staged byte serves up to 32
+//                       DMs.
 //
 // Arithmetic: the sum is a pure integer add of bytes (no tensor-core
-// contraction exists here).  Each thread owns 4 DMs x 16 samples.  A loaded
-// word (4 consecutive samples of one channel) is split into two words of two
-// 16-bit lanes (even samples: AND 0x00FF00FF; odd samples: byte permute), and
-// two channels are added per 3-input integer add, i.e. four byte-adds per
-// instruction.  16-bit lanes hold at most 257 byte sums exactly, so every
-// 256 channels the lanes are widened into 32-bit accumulators.  The result
-// is exact and bit-identical to the definition.
-#include <cstdio>
-
+// contraction exists here).  Each thread owns 4 DMs x 16 samples.  For every
+// group of four channels it loads one word (4 consecutive samples) per
+// channel, transposes the 4x4 bytes with byte permutes, and adds each
+// 4-channel word into an int32 accumulator with one 4-way byte dot product:
+// four channel adds per instruction, exact (every sum is at most 255*nchan).
 #include "sp_internal.h"
 
 namespace sp {
 namespace {
 
-constexpr int kTrTime = 64;
-constexpr int kTrChan = 64;
+constexpr int kStTime = 64;
+constexpr int kStChan = 64;
 
-// 64 samples x 64 channels per CTA through shared memory.  Rows of the
-// output beyond n_in (up to the pitch) are written as zeros.
-__global__ void __launch_bounds__(256) transpose_u8_kernel(const uint8_t *__restrict__ in,
-                                                           int64_t n_in, int32_t nchan,
-                                                           uint8_t *__restrict__ xt,
-                                                           int64_t pitch) {
-    __shared__ __align__(16) uint8_t tile[kTrTime][kTrChan + 4];
-    const int64_t t0 = (int64_t)blockIdx.x * kTrTime;
-    const int c0 = blockIdx.y * kTrChan;
+// 64 samples x 64 channels per CTA through shared memory.  Positions of the
+// output at and past n_in (up to the pitch) are written as zeros.
+__global__ void __launch_bounds__(256) stage_input_kernel(const uint8_t *__restrict__ in, int64_t n_in,
+                                                          int32_t nchan, uint8_t *__restrict__ xt,
+                                                          int64_t pitch) {
+    __shared__ __align__(16) uint8_t tile[kStTime][kStChan + 4];
+    const int64_t t0 = (int64_t)blockIdx.x * kStTime;
+    const int c0 = blockIdx.y * kStChan;
     {
         const int r = threadIdx.x >> 2;
         const int g = (threadIdx.x & 3) * 16;
@@ -63,45 +61,117 @@ __global__ void __launch_bounds__(256) transpose_u8_kernel(const uint8_t *__rest
         dst[0] = v[0]; dst[1] = v[1]; dst[2] = v[2]; dst[3] = v[3];
     }
     __syncthreads();
-    {
-        const int cc = threadIdx.x >> 2;
-        const int tg = (threadIdx.x & 3) * 16;
-        if (c0 + cc < nchan) {
-            uint32_t w[4];
+    const int cc = threadIdx.x >> 2;
+    const int tg = (threadIdx.x & 3) * 16;
+    if (c0 + cc < nchan) {
+        uint32_t w[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                w[q] = (uint32_t)tile[tg + 4 * q + 0][cc] | ((uint32_t)tile[tg + 4 * q + 1][cc] << 8) |
-                       ((uint32_t)tile[tg + 4 * q + 2][cc] << 16) | ((uint32_t)tile[tg + 4 * q + 3][cc] << 24);
-            }
-            *reinterpret_cast<uint4 *>(xt + (int64_t)(c0 + cc) * pitch + t0 + tg) =
-                make_uint4(w[0], w[1], w[2], w[3]);
+        for (int q = 0; q < 4; ++q) {
+            w[q] = (uint32_t)tile[tg + 4 * q + 0][cc] | ((uint32_t)tile[tg + 4 * q + 1][cc] << 8) |
+                   ((uint32_t)tile[tg + 4 * q + 2][cc] << 16) | ((uint32_t)tile[tg + 4 * q + 3][cc] << 24);
         }
+        *reinterpret_cast<uint4 *>(xt + (int64_t)(c0 + cc) * pitch + t0 + tg) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
-// Smem layout of one channel chunk: offset table [CH][DT] int32, then for
-// each channel of the chunk four shifted copies of R_c bytes each.  Copy r,
-// word j = staged bytes [4j + r, 4j + r + 4).
+// ---- TMA (bulk async copy) and mbarrier helpers (inline PTX, sm_90+) ----
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait: gives up after ~2^31 SM cycles (about a second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+    return true;
+}
+// 1-D bulk copy global -> shared, completion counted on `bar` (bytes and
+// both addresses 16-byte multiples).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Shared-memory layout (bytes):
+//   [0, 16)                    two mbarriers, one per staging buffer
+//   [16, 16 + 2*CH*16)         geometry of two chunks (window start, R, copies offset)
+//   [512, 512 + 2*CH*DT*4)     offset tables of two chunks
+//   then copies[2][copies_max] per channel four copies of stride S = R + 16:
+//                              copy r, word j = staged bytes [4j + r, 4j + r + 4).
+//                              Copy 0 is the staged row itself (written by TMA).
+//
+// Pipeline per CTA, one CTA barrier per chunk.  Iteration k:
+//   1. warp 0 issues the bulk copies of chunk k+1 (rows into the copy-0 slots
+//      of buffer (k+1) & 1, plus its offset table) on mbarrier (k+1) & 1 and
+//      publishes the geometry of chunk k+2;
+//   2. every warp sums chunk k from buffer k & 1;
+//   3. every warp waits for chunk k+1's bytes and derives copies 1..3 of its
+//      channel from copy 0;
+//   4. barrier (also the point where a staging time-out is agreed on).
+// A buffer is refilled only after the barrier that follows its last reader.
+//
+// Summation: for four channels a..d of a chunk and one trial DM, each thread
+// loads one aligned word per channel (4 consecutive samples, from the copy
+// that matches the channel's delay modulo 4), transposes the 4x4 bytes with
+// byte permutes so that word j holds sample j of the four channels, and adds
+// each word into sample j's int32 accumulator with one 4-way byte dot
+// product (dp4a against 0x01010101): four channel adds per instruction.
+__device__ __forceinline__ void add_quad(uint32_t wa, uint32_t wb, uint32_t wc, uint32_t wd, int32_t *acc) {
+    const uint32_t t0 = __byte_perm(wa, wb, 0x5140), t1 = __byte_perm(wa, wb, 0x7362);
+    const uint32_t t2 = __byte_perm(wc, wd, 0x5140), t3 = __byte_perm(wc, wd, 0x7362);
+    acc[0] = (int32_t)__dp4a(__byte_perm(t0, t2, 0x5410), 0x01010101u, (uint32_t)acc[0]);
+    acc[1] = (int32_t)__dp4a(__byte_perm(t0, t2, 0x7632), 0x01010101u, (uint32_t)acc[1]);
+    acc[2] = (int32_t)__dp4a(__byte_perm(t1, t3, 0x5410), 0x01010101u, (uint32_t)acc[2]);
+    acc[3] = (int32_t)__dp4a(__byte_perm(t1, t3, 0x7632), 0x01010101u, (uint32_t)acc[3]);
+}
+
 template <int NDT, int NWARP, int CH>
 __global__ void __launch_bounds__(NWARP * 32, 2)
-dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, const int32_t *__restrict__ delays,
-                  int32_t nchan, const int32_t *__restrict__ tile_first,
-                  const int32_t *__restrict__ tile_count, const int32_t *__restrict__ tile_dlo,
-                  const int32_t *__restrict__ tile_span, int64_t n_out, int32_t *__restrict__ out) {
+dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, int32_t nchunks,
+                  const int32_t *__restrict__ tile_first, const int32_t *__restrict__ tile_count,
+                  const int4 *__restrict__ chunk_geo, const int32_t *__restrict__ chunk_off, int32_t copies_max,
+                  int64_t n_out, int32_t *__restrict__ out, int32_t *__restrict__ status) {
     static_assert(NDT == 4, "offset table is read as int4 per thread");
     constexpr int DT = NDT * NWARP;
     constexpr int T = kDedispTimeTile;
-    constexpr int NTHR = NWARP * 32;
-    constexpr int THR_PER_CH = NTHR / CH;
     static_assert(T == 32 * 16, "a warp spans the time tile: 32 lanes x 16 samples");
-    constexpr int kFlushChunks = 256 / CH;
+    static_assert(CH <= 31 && NWARP == CH && CH % 4 == 0, "warp 0 lanes issue one channel each; one warp per channel");
+    static_assert(DT == kDedispDmTile && CH == kDedispChanChunk, "layout shared with the plan");
 
-    extern __shared__ __align__(16) uint8_t smem[];
-    int32_t *offtab = reinterpret_cast<int32_t *>(smem);
-    uint8_t *stage = smem + CH * DT * 4;
-    __shared__ int64_t s_base[CH];
-    __shared__ int32_t s_R[CH];
-    __shared__ int32_t s_off[CH];
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    int4 *geo_s = reinterpret_cast<int4 *>(smem + kDedispGeoOffset);           // [2][CH]
+    int32_t *offt_s = reinterpret_cast<int32_t *>(smem + kDedispOffTabOffset);  // [2][CH*DT]
+    uint8_t *cop_s = smem + kDedispHeaderBytes;                                 // [2][copies_max]
 
     const int tile = blockIdx.x;
     const int64_t t0 = (int64_t)blockIdx.y * T;
@@ -110,134 +180,151 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, const int32_t *
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const bool warp_active = warp * NDT < d_cnt;
+    const int4 *geo_g = chunk_geo + (int64_t)tile * nchunks * CH;
+    const int32_t *off_g = chunk_off + (int64_t)tile * nchunks * CH * DT;
+    const int4 zero4 = make_int4(0, 0, 0, 0);
 
-    uint32_t acc16[NDT][4][2];
-    int32_t acc32[NDT][16];
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // Warp 0: bulk copies of chunk kk (g = the lane's channel geometry).
+    auto issue = [&](int kk, int4 g) {
+        const int b = kk & 1;
+        const int nc = min(CH, nchan - kk * CH);
+        uint32_t bytes = (lane < nc) ? (uint32_t)g.y + 16u : 0u;
 #pragma unroll
-    for (int i = 0; i < NDT; ++i) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc16[i][k][0] = acc16[i][k][1] = 0u;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc32[i][j] = 0;
+        for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+        fence_proxy_async();
+        if (lane == 0) mbar_arrive_expect_tx(&mbar[b], bytes + (uint32_t)(CH * DT * 4));
+        __syncwarp();
+        if (lane < nc)
+            bulk_g2s(cop_s + b * copies_max + g.z, xt + (int64_t)(kk * CH + lane) * pitch + t0 + g.x,
+                     (uint32_t)g.y + 16u, &mbar[b]);
+        if (lane == CH) bulk_g2s(offt_s + b * CH * DT, off_g + (int64_t)kk * CH * DT, CH * DT * 4, &mbar[b]);
+    };
+    auto load_geo = [&](int kk) -> int4 {
+        return (kk < nchunks && lane < CH && kk * CH + lane < nchan) ? __ldg(geo_g + (int64_t)kk * CH + lane)
+                                                                      : zero4;
+    };
+    // Derive copies 1..3 of this warp's channel of chunk kk (buffer b) from copy 0.
+    auto build = [&](int kk, int b) {
+        if (kk * CH + warp >= nchan) return;
+        const int4 g = geo_s[b * CH + warp];
+        const int32_t R = g.y, S = g.y + 16;
+        uint8_t *row = cop_s + b * copies_max + g.z;
+        const int nseg = R / 16;
+        for (int q0 = 0; q0 < nseg; q0 += 32) {
+            const int q = q0 + lane;
+            const bool act = q < nseg;
+            uint4 a = make_uint4(0u, 0u, 0u, 0u);
+            if (act) a = *reinterpret_cast<const uint4 *>(row + 16 * q);
+            uint32_t e = __shfl_down_sync(0xffffffffu, a.x, 1);
+            if (act && (lane == 31 || q + 1 >= nseg)) e = *reinterpret_cast<const uint32_t *>(row + 16 * q + 16);
+            if (act) {
+                *reinterpret_cast<uint4 *>(row + S + 16 * q) =
+                    make_uint4(__byte_perm(a.x, a.y, 0x4321), __byte_perm(a.y, a.z, 0x4321),
+                               __byte_perm(a.z, a.w, 0x4321), __byte_perm(a.w, e, 0x4321));
+                *reinterpret_cast<uint4 *>(row + 2 * S + 16 * q) =
+                    make_uint4(__byte_perm(a.x, a.y, 0x5432), __byte_perm(a.y, a.z, 0x5432),
+                               __byte_perm(a.z, a.w, 0x5432), __byte_perm(a.w, e, 0x5432));
+                *reinterpret_cast<uint4 *>(row + 3 * S + 16 * q) =
+                    make_uint4(__byte_perm(a.x, a.y, 0x6543), __byte_perm(a.y, a.z, 0x6543),
+                               __byte_perm(a.z, a.w, 0x6543), __byte_perm(a.w, e, 0x6543));
+            }
+        }
+    };
+
+    // Prologue: stage chunk 0 and derive its copies; publish chunk 1's geometry.
+    int4 g_k1 = zero4, g_k2 = zero4;
+    if (warp == 0) {
+        const int4 g0 = load_geo(0);
+        g_k1 = load_geo(1);
+        g_k2 = load_geo(2);
+        if (lane < CH) {
+            geo_s[lane] = g0;
+            geo_s[CH + lane] = g_k1;
+        }
+        issue(0, g0);
+    }
+    __syncthreads();
+    {
+        const bool ok = mbar_wait_bounded(&mbar[0], 0u);
+        if (ok) build(0, 0);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(status, SP_STATUS_STAGING_TIMEOUT);
+            return;
+        }
     }
 
-    int chunks_since_flush = 0;
-    for (int c0 = 0; c0 < nchan; c0 += CH) {
-        const int nc = min(CH, nchan - c0);
-        if (threadIdx.x < CH) {
-            const int c = threadIdx.x;
-            int32_t R = 0;
-            int64_t base = 0;
-            if (c < nc) {
-                const int64_t idx = (int64_t)tile * nchan + c0 + c;
-                base = (t0 + tile_dlo[idx]) & ~int64_t(15);
-                R = dedisp_row_bytes(tile_span[idx]);
-            }
-            s_base[c] = base;
-            s_R[c] = R;
+    int32_t acc[NDT][16];
+#pragma unroll
+    for (int i = 0; i < NDT; ++i)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[i][j] = 0;
+
+    for (int k = 0; k < nchunks; ++k) {
+        const int b = k & 1;
+        const int nc = min(CH, nchan - k * CH);
+        if (warp == 0 && k + 1 < nchunks) {
+            issue(k + 1, g_k1);
+            if (lane < CH) geo_s[b * CH + lane] = g_k2;  // chunk k+2 lives in buffer b
+            g_k1 = g_k2;
+            g_k2 = load_geo(k + 3);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int32_t acc = 0;
-            for (int c = 0; c < CH; ++c) {
-                s_off[c] = acc;
-                acc += 4 * s_R[c];
-            }
-        }
-        __syncthreads();
-        // Offset of each (channel, DM) in the staged copies; DM slots past
-        // the tile's count reuse the last valid DM (their sums are dropped).
-        for (int i = threadIdx.x; i < CH * DT; i += NTHR) {
-            const int c = i / DT;
-            const int dl = i - c * DT;
-            int32_t off = 0;
-            if (c < nc) {
-                const int dd = min(dl, d_cnt - 1);
-                const int32_t dly = __ldg(delays + (int64_t)(d_first + dd) * nchan + c0 + c);
-                const int32_t shift = (int32_t)(t0 + dly - s_base[c]);
-                off = s_off[c] + (shift & 3) * s_R[c] + (shift & ~3);
-            }
-            offtab[i] = off;
-        }
-        // Stage: THR_PER_CH threads per channel, 16 input bytes per step.
-        {
-            const int c = threadIdx.x / THR_PER_CH;
-            const int j = threadIdx.x - c * THR_PER_CH;
-            if (c < nc) {
-                const int32_t R = s_R[c];
-                const uint8_t *src = xt + (int64_t)(c0 + c) * pitch + s_base[c];
-                uint8_t *dst = stage + s_off[c];
-                for (int q = j; q < R / 16; q += THR_PER_CH) {
-                    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(src + 16 * q));
-                    const uint32_t e = __ldg(reinterpret_cast<const uint32_t *>(src + 16 * q + 16));
-                    *reinterpret_cast<uint4 *>(dst + 16 * q) = a;
-                    *reinterpret_cast<uint4 *>(dst + R + 16 * q) =
-                        make_uint4(__byte_perm(a.x, a.y, 0x4321), __byte_perm(a.y, a.z, 0x4321),
-                                   __byte_perm(a.z, a.w, 0x4321), __byte_perm(a.w, e, 0x4321));
-                    *reinterpret_cast<uint4 *>(dst + 2 * R + 16 * q) =
-                        make_uint4(__byte_perm(a.x, a.y, 0x5432), __byte_perm(a.y, a.z, 0x5432),
-                                   __byte_perm(a.z, a.w, 0x5432), __byte_perm(a.w, e, 0x5432));
-                    *reinterpret_cast<uint4 *>(dst + 3 * R + 16 * q) =
-                        make_uint4(__byte_perm(a.x, a.y, 0x6543), __byte_perm(a.y, a.z, 0x6543),
-                                   __byte_perm(a.z, a.w, 0x6543), __byte_perm(a.w, e, 0x6543));
-                }
-            }
-        }
-        __syncthreads();
 
         if (warp_active) {
-            const uint8_t *sb = stage + lane * 4;
-            const int32_t *ot = offtab + warp * NDT;
-            int c = 0;
-            for (; c + 1 < nc; c += 2) {
-                const int4 oa = *reinterpret_cast<const int4 *>(ot + c * DT);
-                const int4 ob = *reinterpret_cast<const int4 *>(ot + (c + 1) * DT);
-                const int32_t oas[4] = {oa.x, oa.y, oa.z, oa.w};
-                const int32_t obs[4] = {ob.x, ob.y, ob.z, ob.w};
+            const uint8_t *sb = cop_s + b * copies_max + lane * 4;
+            const int32_t *ot = offt_s + b * CH * DT + warp * NDT;
+            if (nc == CH) {
 #pragma unroll
-                for (int i = 0; i < NDT; ++i) {
-                    const uint8_t *pa = sb + oas[i];
-                    const uint8_t *pb = sb + obs[i];
+                for (int qd = 0; qd < CH / 4; ++qd) {
+                    const int4 o0 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 0) * DT);
+                    const int4 o1 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 1) * DT);
+                    const int4 o2 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 2) * DT);
+                    const int4 o3 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 3) * DT);
+                    const int32_t a0[4] = {o0.x, o0.y, o0.z, o0.w}, a1[4] = {o1.x, o1.y, o1.z, o1.w};
+                    const int32_t a2[4] = {o2.x, o2.y, o2.z, o2.w}, a3[4] = {o3.x, o3.y, o3.z, o3.w};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * k);
-                        const uint32_t wb = *reinterpret_cast<const uint32_t *>(pb + 128 * k);
-                        acc16[i][k][0] += (wa & 0x00FF00FFu) + (wb & 0x00FF00FFu);
-                        acc16[i][k][1] += __byte_perm(wa, 0u, 0x4341) + __byte_perm(wb, 0u, 0x4341);
+                    for (int i = 0; i < NDT; ++i) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t wa = *reinterpret_cast<const uint32_t *>(sb + a0[i] + 128 * q);
+                            const uint32_t wb = *reinterpret_cast<const uint32_t *>(sb + a1[i] + 128 * q);
+                            const uint32_t wc = *reinterpret_cast<const uint32_t *>(sb + a2[i] + 128 * q);
+                            const uint32_t wd = *reinterpret_cast<const uint32_t *>(sb + a3[i] + 128 * q);
+                            add_quad(wa, wb, wc, wd, &acc[i][4 * q]);
+                        }
                     }
                 }
-            }
-            if (c < nc) {
-                const int4 oa = *reinterpret_cast<const int4 *>(ot + c * DT);
-                const int32_t oas[4] = {oa.x, oa.y, oa.z, oa.w};
+            } else {
+                // Last, partial chunk: one channel at a time.
+                for (int c = 0; c < nc; ++c) {
+                    const int4 oc = *reinterpret_cast<const int4 *>(ot + c * DT);
+                    const int32_t ac[4] = {oc.x, oc.y, oc.z, oc.w};
 #pragma unroll
-                for (int i = 0; i < NDT; ++i) {
-                    const uint8_t *pa = sb + oas[i];
+                    for (int i = 0; i < NDT; ++i) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * k);
-                        acc16[i][k][0] += wa & 0x00FF00FFu;
-                        acc16[i][k][1] += __byte_perm(wa, 0u, 0x4341);
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t w = *reinterpret_cast<const uint32_t *>(sb + ac[i] + 128 * q);
+                            add_quad(w, 0u, 0u, 0u, &acc[i][4 * q]);
+                        }
                     }
                 }
             }
         }
-        __syncthreads();
 
-        if (++chunks_since_flush == kFlushChunks || c0 + CH >= nchan) {
-            chunks_since_flush = 0;
-#pragma unroll
-            for (int i = 0; i < NDT; ++i) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t e = acc16[i][k][0], o = acc16[i][k][1];
-                    acc32[i][4 * k + 0] += (int32_t)(e & 0xFFFFu);
-                    acc32[i][4 * k + 2] += (int32_t)(e >> 16);
-                    acc32[i][4 * k + 1] += (int32_t)(o & 0xFFFFu);
-                    acc32[i][4 * k + 3] += (int32_t)(o >> 16);
-                    acc16[i][k][0] = acc16[i][k][1] = 0u;
-                }
-            }
+        bool ok = true;
+        if (k + 1 < nchunks) {
+            ok = mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
+            if (ok) build(k + 1, b ^ 1);
+        }
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(status, SP_STATUS_STAGING_TIMEOUT);
+            return;
         }
     }
 
@@ -246,37 +333,37 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, const int32_t *
     for (int i = 0; i < NDT; ++i) {
         const int dl = warp * NDT + i;
         if (dl >= d_cnt) continue;
-        int32_t *row = out + (int64_t)(d_first + dl) * n_out;
+        int32_t *orow = out + (int64_t)(d_first + dl) * n_out;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t t = t0 + 128 * k + 4 * lane;
+        for (int q = 0; q < 4; ++q) {
+            const int64_t t = t0 + 128 * q + 4 * lane;
             if (vec && t + 3 < n_out) {
-                *reinterpret_cast<int4 *>(row + t) =
-                    make_int4(acc32[i][4 * k], acc32[i][4 * k + 1], acc32[i][4 * k + 2], acc32[i][4 * k + 3]);
+                *reinterpret_cast<int4 *>(orow + t) =
+                    make_int4(acc[i][4 * q], acc[i][4 * q + 1], acc[i][4 * q + 2], acc[i][4 * q + 3]);
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (t + j < n_out) row[t + j] = acc32[i][4 * k + j];
+                    if (t + j < n_out) orow[t + j] = acc[i][4 * q + j];
             }
         }
     }
 }
 
-using DedispKernel = void (*)(const uint8_t *, int64_t, const int32_t *, int32_t, const int32_t *,
-                              const int32_t *, const int32_t *, const int32_t *, int64_t, int32_t *);
+using DedispKernel = void (*)(const uint8_t *, int64_t, int32_t, int32_t, const int32_t *, const int32_t *,
+                              const int4 *, const int32_t *, int32_t, int64_t, int32_t *, int32_t *);
 constexpr DedispKernel kDedisp = dedisperse_kernel<kDedispDmPerThread, kDedispWarps, kDedispChanChunk>;
 
 }  // namespace
 
-int launch_transpose(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_xt, int64_t pitch,
-                     cudaStream_t stream) {
-    const dim3 grid((unsigned)(pitch / kTrTime), (unsigned)((nchan + kTrChan - 1) / kTrChan));
-    transpose_u8_kernel<<<grid, 256, 0, stream>>>(d_in, n_in, nchan, d_xt, pitch);
+int launch_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_staged, int64_t pitch,
+                       cudaStream_t stream) {
+    const dim3 grid((unsigned)(pitch / kStTime), (unsigned)((nchan + kStChan - 1) / kStChan));
+    stage_input_kernel<<<grid, 256, 0, stream>>>(d_in, n_in, nchan, d_staged, pitch);
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
-int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, int64_t n_out,
-                      int32_t *d_out, cudaStream_t stream) {
+int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, int64_t n_out, int32_t *d_out,
+                      cudaStream_t stream) {
     static int configured_smem[64] = {0};
     const int dev = plan->device < 64 ? plan->device : 63;
     if (configured_smem[dev] < plan->smem_bytes) {
@@ -288,8 +375,8 @@ int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, i
     const int64_t ntime = (n_out + kDedispTimeTile - 1) / kDedispTimeTile;
     const dim3 grid((unsigned)plan->ntiles, (unsigned)ntime);
     kDedisp<<<grid, kDedispWarps * 32, plan->smem_bytes, stream>>>(
-        d_xt, pitch, plan->d_delays, plan->nchan, plan->d_tile_first, plan->d_tile_count, plan->d_tile_dlo,
-        plan->d_tile_span, n_out, d_out);
+        d_xt, pitch, plan->nchan, plan->nchunks, plan->d_tile_first, plan->d_tile_count, plan->d_chunk_geo,
+        plan->d_chunk_off, plan->copies_max, n_out, d_out, plan->d_status);
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

@@ -47,6 +47,56 @@ int compute_delays(const double *freqs, int32_t nchan, double tsamp, const doubl
     return SP_OK;
 }
 
+// Staging tables of the dedispersion kernel, per (DM tile, channel chunk).
+// Time tiles start at multiples of kDedispTimeTile (a multiple of 16), so the
+// 16-byte-aligned window start of a channel relative to the time tile is
+// (min delay over the tile) rounded down to 16 and does not depend on the
+// time tile; neither do the offsets derived from it.  Each channel's four
+// byte-shifted copies have stride R + 16: copy 0 is the staged row itself,
+// 16 bytes longer than the R bytes any copy is read over, so that copies
+// 1..3 can be derived from it.
+void build_chunk_tables(const sp_plan &p, std::vector<int32_t> &geo, std::vector<int32_t> &off,
+                        int32_t *copies_max) {
+    const int32_t CH = kDedispChanChunk, DT = kDedispDmTile;
+    geo.assign((size_t)p.ntiles * p.nchunks * CH * 4, 0);
+    off.assign((size_t)p.ntiles * p.nchunks * CH * DT, 0);
+    int32_t cmax = 0;
+    for (int32_t j = 0; j < p.ntiles; ++j) {
+        const int32_t d0 = p.tile_first[j], cnt = p.tile_count[j];
+        for (int32_t k = 0; k < p.nchunks; ++k) {
+            const int32_t c0 = k * CH;
+            const int32_t nc = std::min(CH, p.nchan - c0);
+            int32_t soff = 0;
+            for (int32_t i = 0; i < nc; ++i) {
+                const int32_t c = c0 + i;
+                int32_t lo = INT32_MAX, hi = 0;
+                for (int32_t dl = 0; dl < cnt; ++dl) {
+                    const int32_t v = p.delays[(size_t)(d0 + dl) * p.nchan + c];
+                    lo = std::min(lo, v);
+                    hi = std::max(hi, v);
+                }
+                const int32_t rel_base = lo & ~15;
+                const int32_t R = dedisp_row_bytes(hi - lo);
+                const int32_t stride = R + 16;
+                int32_t *g = &geo[(((size_t)j * p.nchunks + k) * CH + i) * 4];
+                g[0] = rel_base;
+                g[1] = R;
+                g[2] = soff;
+                g[3] = 0;
+                int32_t *o = &off[(((size_t)j * p.nchunks + k) * CH + i) * DT];
+                for (int32_t dl = 0; dl < DT; ++dl) {
+                    const int32_t dd = std::min(dl, cnt - 1);  // idle slots repeat the last DM
+                    const int32_t shift = p.delays[(size_t)(d0 + dd) * p.nchan + c] - rel_base;
+                    o[dl] = soff + (shift & 3) * stride + (shift & ~3);
+                }
+                soff += 4 * stride;
+            }
+            cmax = std::max(cmax, soff);
+        }
+    }
+    *copies_max = cmax;
+}
+
 }  // namespace sp
 
 using namespace sp;
@@ -55,9 +105,11 @@ static void free_plan_device(sp_plan *p) {
     cudaFree(p->d_delays);
     cudaFree(p->d_tile_first);
     cudaFree(p->d_tile_count);
-    cudaFree(p->d_tile_dlo);
-    cudaFree(p->d_tile_span);
-    p->d_delays = p->d_tile_first = p->d_tile_count = p->d_tile_dlo = p->d_tile_span = nullptr;
+    cudaFree(p->d_chunk_geo);
+    cudaFree(p->d_chunk_off);
+    cudaFree(p->d_status);
+    p->d_delays = p->d_tile_first = p->d_tile_count = p->d_chunk_off = p->d_status = nullptr;
+    p->d_chunk_geo = nullptr;
 }
 
 template <class T>
@@ -89,9 +141,8 @@ extern "C" int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsa
     // most kDedispDmTile members and a per-channel delay spread (max - min
     // over the run) of at most kDedispMaxSpan samples.  A single DM has
     // spread 0, so every plan tiles.
-    std::vector<int32_t> lo(nchan), hi(nchan), tile_dlo, tile_span;
+    std::vector<int32_t> lo(nchan), hi(nchan);
     int32_t d = 0;
-    int32_t worst_chunk = 0;
     while (d < ndm) {
         const int32_t *row = &p->delays[(size_t)d * nchan];
         std::copy(row, row + nchan, lo.begin());
@@ -113,20 +164,13 @@ extern "C" int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsa
         }
         p->tile_first.push_back(d);
         p->tile_count.push_back(cnt);
-        for (int32_t c = 0; c < nchan; ++c) {
-            tile_dlo.push_back(lo[c]);
-            tile_span.push_back(hi[c] - lo[c]);
-        }
-        for (int32_t c0 = 0; c0 < nchan; c0 += kDedispChanChunk) {
-            int32_t bytes = 0;
-            for (int32_t c = c0; c < std::min(nchan, c0 + kDedispChanChunk); ++c)
-                bytes += 4 * dedisp_row_bytes(hi[c] - lo[c]);
-            worst_chunk = std::max(worst_chunk, bytes);
-        }
         d += cnt;
     }
     p->ntiles = (int32_t)p->tile_first.size();
-    p->smem_bytes = worst_chunk + kDedispChanChunk * kDedispDmTile * 4;
+    p->nchunks = (nchan + kDedispChanChunk - 1) / kDedispChanChunk;
+    std::vector<int32_t> geo, off;
+    build_chunk_tables(*p, geo, off, &p->copies_max);
+    p->smem_bytes = kDedispHeaderBytes + 2 * p->copies_max;
 
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         cudaGetLastError();
@@ -136,8 +180,10 @@ extern "C" int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsa
     rc = upload(&p->d_delays, p->delays.data(), p->delays.size());
     if (!rc) rc = upload(&p->d_tile_first, p->tile_first.data(), p->tile_first.size());
     if (!rc) rc = upload(&p->d_tile_count, p->tile_count.data(), p->tile_count.size());
-    if (!rc) rc = upload(&p->d_tile_dlo, tile_dlo.data(), tile_dlo.size());
-    if (!rc) rc = upload(&p->d_tile_span, tile_span.data(), tile_span.size());
+    if (!rc) rc = upload(reinterpret_cast<int32_t **>(&p->d_chunk_geo), geo.data(), geo.size());
+    if (!rc) rc = upload(&p->d_chunk_off, off.data(), off.size());
+    const int32_t zero = 0;
+    if (!rc) rc = upload(&p->d_status, &zero, 1);
     if (rc) {
         free_plan_device(p);
         delete p;
@@ -171,6 +217,14 @@ extern "C" int sp_compute_delays(const double *freqs_mhz, int32_t nchan, double 
     if (rc) return rc;
     std::memcpy(h_out, tab.data(), tab.size() * sizeof(int32_t));
     if (max_delay) *max_delay = mx;
+    return SP_OK;
+}
+
+extern "C" int sp_plan_status(const sp_plan *p, int32_t *h_status, int32_t clear) {
+    if (!p || !h_status) return SP_EINVAL;
+    if (cudaMemcpy(h_status, p->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SP_ECUDA;
+    if (clear && cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) return SP_ECUDA;
     return SP_OK;
 }
 

@@ -16,16 +16,22 @@ constexpr int kDedispDmPerThread = 4;                     // trial DMs per threa
 constexpr int kDedispWarps = 8;                           // warps per CTA
 constexpr int kDedispDmTile = kDedispDmPerThread * kDedispWarps;  // 32 DMs per CTA
 constexpr int kDedispTimeTile = 512;                      // output samples per CTA
-constexpr int kDedispChanChunk = 16;                      // channels staged per pass
+constexpr int kDedispChanChunk = 8;                       // channels staged per pass
 constexpr int kDedispMaxSpan = 1024;                      // max delay spread in a DM tile
-// Channel-major workspace row pitch: room for a full time tile and the
-// 16-byte staging overrun past n_in, rounded to 64 bytes.
+// Shared-memory header of the dedispersion kernel: two mbarriers, the
+// geometry of two chunks, and two (channel, DM) offset tables.
+constexpr int kDedispGeoOffset = 16;
+constexpr int kDedispOffTabOffset = 512;
+constexpr int kDedispOffTabInts = kDedispChanChunk * kDedispDmTile;
+constexpr int kDedispHeaderBytes = kDedispOffTabOffset + 2 * kDedispOffTabInts * 4;
+// Staged-input row pitch: room for the last time tile's window past n_in,
+// rounded to 64 bytes.
 __host__ __device__ inline int64_t dedisp_pitch(int64_t n_in) {
     return ((n_in + kDedispTimeTile + 64 + 63) / 64) * 64;
 }
-// Staged bytes of one channel for a tile whose delay spread is `span`:
-// four byte-shifted copies of a window that covers the time tile, the spread
-// and the 16-byte alignment slack.
+// Bytes of one shifted copy of one channel for a tile whose delay spread is
+// `span`: a window that covers the time tile, the spread and the 16-byte
+// alignment slack of its start.
 __host__ __device__ inline int32_t dedisp_row_bytes(int32_t span) {
     return ((15 + span + kDedispTimeTile + 15) / 16) * 16;
 }
@@ -40,14 +46,21 @@ struct sp_plan {
     // DM tiles: consecutive runs of at most kDedispDmTile trial DMs whose
     // per-channel delay spread stays within kDedispMaxSpan.
     int32_t ntiles = 0;
+    int32_t nchunks = 0;          // channel chunks of kDedispChanChunk
     std::vector<int32_t> tile_first, tile_count;
+    int32_t copies_max = 0;       // largest shifted-copy staging of one chunk (bytes)
     int32_t smem_bytes = 0;       // dynamic shared memory of the dedispersion kernel
     // device copies
     int32_t *d_delays = nullptr;      // [ndm][nchan]
     int32_t *d_tile_first = nullptr;  // [ntiles]
     int32_t *d_tile_count = nullptr;  // [ntiles]
-    int32_t *d_tile_dlo = nullptr;    // [ntiles][nchan] min delay over the tile
-    int32_t *d_tile_span = nullptr;   // [ntiles][nchan] max - min delay over the tile
+    // Per (tile, chunk, channel): {window start relative to the time tile,
+    // bytes R read from one copy, offset of the channel's copies, 0}.
+    int4 *d_chunk_geo = nullptr;      // [ntiles][nchunks][kDedispChanChunk]
+    // Per (tile, chunk, channel, DM): byte offset of the DM's first sample in
+    // the chunk's copies (copy (shift & 3), word shift >> 2).
+    int32_t *d_chunk_off = nullptr;   // [ntiles][nchunks][kDedispChanChunk][kDedispDmTile]
+    int32_t *d_status = nullptr;      // device status word (bit 0: a staging wait timed out)
 };
 
 namespace sp {
@@ -57,10 +70,13 @@ int compute_delays(const double *freqs, int32_t nchan, double tsamp, const doubl
                    int32_t ndm, std::vector<int32_t> &out, int32_t *max_delay);
 
 // Kernel launchers (return SP_OK or SP_ECUDA).
-int launch_transpose(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_xt,
-                     int64_t pitch, cudaStream_t stream);
+int launch_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_staged,
+                       int64_t pitch, cudaStream_t stream);
 int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, int64_t n_out,
                       int32_t *d_out, cudaStream_t stream);
+// Host-side layout of the per-(tile, chunk) staging tables (plan.cpp).
+void build_chunk_tables(const sp_plan &p, std::vector<int32_t> &geo, std::vector<int32_t> &off,
+                        int32_t *copies_max);
 
 struct SpsArgs {
     const int32_t *dmt;

@@ -262,9 +262,10 @@ def test_config2_search_sampled(config2_run):
     assert found >= len(bursts) // 2, (found, len(bursts))
 
 
-def test_channel_major_entry_points():
-    """transpose + dedisperse_cm equals dedisperse; bytes past n_in in a
-    channel-major row do not affect the result; the probe reports a sane rate."""
+def test_staged_entry_points():
+    """stage_input + dedisperse_staged equals dedisperse; the staged form is
+    the zero-padded channel-major input; the probe reports a sane rate; the
+    plan's device status stays clear."""
     rng = np.random.default_rng(21)
     f = synth.band_freqs(80)
     dms = np.arange(70, dtype=np.float64) * 1.3
@@ -274,17 +275,15 @@ def test_channel_major_entry_points():
     x = rng.integers(0, 256, size=(n_in, 80), dtype=np.uint8)
     ref = gu.dev_dedisperse(plan, x)
     d_in = torch.from_numpy(x).cuda()
-    pitch = sp.cm_pitch(n_in)
-    xt = torch.empty((80, pitch), dtype=torch.uint8, device="cuda")
-    sp.transpose_to_cm(d_in, xt)
+    xt = sp.staged_buffer(80, n_in)
+    sp.stage_input(d_in, xt)
     out = torch.empty_like(ref)
-    sp.dedisperse_cm(plan, xt, n_in, out)
+    sp.dedisperse_staged(plan, xt, n_in, out)
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
-    assert torch.equal(xt[:, :n_in].cpu(), torch.from_numpy(np.ascontiguousarray(x.T)))
-    xt[:, n_in:] = 255  # garbage past the input must not matter
-    sp.dedisperse_cm(plan, xt, n_in, out)
-    torch.cuda.synchronize()
-    assert torch.equal(out, ref)
+    pitch = sp.staged_pitch(n_in)
+    xs = xt.cpu().numpy()[: 80 * pitch].reshape(80, pitch)
+    assert np.array_equal(xs[:, :n_in], x.T) and not xs[:, n_in:].any()
     rate, nsm = sp.probe_iadd3_rate(256)
     assert nsm >= 100 and 16 <= rate <= 160
+    assert plan.status() == 0

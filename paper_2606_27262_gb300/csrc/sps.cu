@@ -5,23 +5,28 @@
 //
 // Kernels:
 //   sps_stats_kernel   one CTA per (row, normalisation block): exact int64
-//                      sum and sum of squares, the 128-bit variance term, and
-//                      per-width float coefficients of the S/N affine map.
+//                      sum and sum of squares (16-byte loads), the 128-bit
+//                      variance term, and per-width float coefficients of
+//                      the S/N affine map.
 //   sps_boxcar_kernel  one CTA per 14 rows x 256 samples (+1 halo row and
-//                      sample on each side).  Stages int64 prefix sums of the
-//                      rows in shared memory (warp-shuffle scans), evaluates
-//                      every width for every (row, sample), keeps the best,
-//                      then applies the threshold and the 3x3 rule from the
-//                      staged best-S/N tile and appends candidates with one
-//                      atomic per warp.  A template switch writes the best-S/N
-//                      map instead of candidates.
+//                      sample on each side).  Stages prefix sums of the rows
+//                      in shared memory (warp-shuffle scans), evaluates every
+//                      width for every (row, sample), keeps the best, then
+//                      applies the threshold and the 3x3 rule from the staged
+//                      best-S/N tile and appends candidates with one atomic
+//                      per warp.  A template switch writes the best-S/N map
+//                      instead of candidates.
 //
 // S/N arithmetic.  For block b of row d with count n, sum Sx, sum of squares
 // Sxx, let m0 = floor(Sx/n) and f = Sx/n - m0.  For a window sum S of width w
 //   snr = (n*S - w*Sx) / (sqrt(w)*sqrt(n*Sxx - Sx^2))
 //       = ((S - w*m0) - w*f) * inv_w,   inv_w = n / (sqrt(w)*sqrt(V)).
-// S - w*m0 is formed exactly in int64 from the prefix sums; only the final
-// conversion to float and one fused multiply-add round.
+// x = S - w*m0 is an exact integer; only its conversion to float and one
+// fused multiply-add round.  x is formed from 32-bit prefix sums with
+// wrap-around arithmetic: the result is exact whenever |x| < 2^31, which the
+// kernel proves per CTA from the staged values (|x| <= w * max|v - m0|);
+// 8-bit beams of up to 8192 channels always qualify.  A CTA that cannot
+// prove it evaluates the same formula in 64-bit integers instead.
 #include <cmath>
 
 #include "sp_internal.h"
@@ -51,7 +56,22 @@ __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restric
     const int64_t hi = (b == nblk - 1) ? n_out : (b + 1) * norm_block;
     const int32_t *row = dmt + d * n_out;
     int64_t s1 = 0, s2 = 0;
-    for (int64_t t = lo + threadIdx.x; t < hi; t += 256) {
+    // Scalar head up to a 16-byte boundary, 16-byte body, scalar tail.
+    const int64_t head = min(hi, lo + (int64_t)((4 - (((uintptr_t)(row + lo) >> 2) & 3)) & 3));
+    const int64_t nvec = (hi - head) / 4;
+    for (int64_t t = lo + threadIdx.x; t < head; t += 256) {
+        const int64_t x = __ldg(row + t);
+        s1 += x;
+        s2 += x * x;
+    }
+    const int4 *vrow = reinterpret_cast<const int4 *>(row + head);
+    for (int64_t i = threadIdx.x; i < nvec; i += 256) {
+        const int4 q = __ldg(vrow + i);
+        const int64_t a = q.x, bb = q.y, c = q.z, e = q.w;
+        s1 += a + bb + c + e;
+        s2 += a * a + bb * bb + c * c + e * e;
+    }
+    for (int64_t t = head + 4 * nvec + threadIdx.x; t < hi; t += 256) {
         const int64_t x = __ldg(row + t);
         s1 += x;
         s2 += x * x;
@@ -91,6 +111,105 @@ constexpr int kBxIn = kBxRows - 2;
 constexpr int kBxTT = kBxT + 2;           // staged samples incl. halo
 constexpr int kBxPerLane = (kBxTT + 31) / 32;
 
+// Best S/N over the widths at staged sample ti of one row, from prefix sums
+// P (uint32 wrap-around or int64).  cw[k] = w_k * m0 in the same type.
+// Windows must end by staged index fit_end (exclusive).
+template <typename PT>
+__device__ __forceinline__ void best_over_widths(const PT *Pr, int ti, int fit_end, const WidthList &wl,
+                                                 const PT *cw, const float2 *cf, float &best, int &kb) {
+    const PT p0 = Pr[ti];
+#pragma unroll
+    for (int k = 0; k < SP_MAX_WIDTHS; ++k) {
+        if (k >= wl.nw) break;
+        const int w = wl.w[k];
+        if (ti + w > fit_end) break;  // widths increase: no later one fits either
+        const PT xs = Pr[ti + w] - p0 - cw[k];
+        float xf;
+        if constexpr (sizeof(PT) == 4)
+            xf = (float)(int32_t)xs;  // exact value of x: |x| < 2^31 was checked
+        else
+            xf = (float)(int64_t)xs;
+        const float s = fmaf(xf, cf[k].x, -cf[k].y);
+        if (s > best) {
+            best = s;
+            kb = k;
+        }
+    }
+}
+
+// Phase 1 for one row: P[i] = sum_{j<i} v(tbase + j) for i in [0, LP], with
+// staged indices outside [i_lo, i_hi) read as zero; also the min/max of the
+// staged values.
+template <typename PT>
+__device__ __forceinline__ void prefix_row(const int32_t *__restrict__ row, int64_t tbase, int LP, int i_lo,
+                                           int i_hi, PT *Pr, int32_t &vmin, int32_t &vmax) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) Pr[0] = 0;
+    PT carry = 0;
+    for (int base = 0; base < LP; base += 32) {
+        const int i = base + lane;
+        int32_t x = 0;
+        if (i >= i_lo && i < i_hi) {
+            x = __ldg(row + (tbase + i));
+            vmin = min(vmin, x);
+            vmax = max(vmax, x);
+        }
+        PT v = (PT)x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const PT u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (i < LP) Pr[i + 1] = carry + v;
+        carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+}
+
+// Phase 2 for one row: best S/N and width of every staged sample.
+template <typename PT>
+__device__ __forceinline__ void score_row(const PT *Pr, int d, int64_t tbase, int i_lo, int i_hi, int fit_end,
+                                          const WidthList &wl, int64_t norm_block, int64_t nblk,
+                                          const int32_t *__restrict__ m0s, const float2 *__restrict__ coefs,
+                                          float *snr_row, int8_t *k_row) {
+    const int lane = threadIdx.x & 31;
+    const int ti0 = lane * kBxPerLane;
+    int next_edge = -1;  // staged index where the next normalisation block starts
+    PT cw[SP_MAX_WIDTHS];
+    float2 cf[SP_MAX_WIDTHS];
+#pragma unroll
+    for (int k = 0; k < SP_MAX_WIDTHS; ++k) {
+        cw[k] = 0;
+        cf[k] = make_float2(0.f, 0.f);
+    }
+    for (int j = 0; j < kBxPerLane; ++j) {
+        const int ti = ti0 + j;
+        if (ti >= kBxTT) break;
+        float best = -INFINITY;
+        int kb = -1;
+        if (ti >= i_lo && ti < i_hi) {
+            if (ti >= next_edge) {
+                const int64_t t = tbase + ti;
+                int64_t b = (norm_block > 0) ? t / norm_block : 0;
+                if (b > nblk - 1) b = nblk - 1;
+                const int64_t edge = (b == nblk - 1) ? INT64_MAX : (b + 1) * norm_block;
+                next_edge = (int)min(edge - tbase, (int64_t)INT32_MAX);
+                const int64_t idx = (int64_t)d * nblk + b;
+                const PT m0 = (PT)(int64_t)__ldg(m0s + idx);
+#pragma unroll
+                for (int k = 0; k < SP_MAX_WIDTHS; ++k) {
+                    if (k < wl.nw) {
+                        cw[k] = (PT)wl.w[k] * m0;
+                        cf[k] = __ldg(coefs + idx * wl.nw + k);
+                    }
+                }
+            }
+            best_over_widths<PT>(Pr, ti, fit_end, wl, cw, cf, best, kb);
+        }
+        snr_row[ti] = best;
+        k_row[ti] = (int8_t)kb;
+    }
+}
+
 template <bool MAP>
 __global__ void __launch_bounds__(256, 2)
 sps_boxcar_kernel(const int32_t *__restrict__ dmt, int32_t ndm, int64_t n_out, WidthList wl, int32_t maxw,
@@ -100,34 +219,54 @@ sps_boxcar_kernel(const int32_t *__restrict__ dmt, int32_t ndm, int64_t n_out, W
                   int8_t *__restrict__ map_k) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int LP = kBxTT + maxw;  // prefix entries 0..LP
-    int64_t *P = reinterpret_cast<int64_t *>(smem);
     float *snr_s = reinterpret_cast<float *>(smem + (size_t)kBxRows * (LP + 1) * 8);
     int8_t *k_s = reinterpret_cast<int8_t *>(snr_s + kBxRows * kBxTT);
+    uint32_t *P32 = reinterpret_cast<uint32_t *>(smem);
+    int64_t *P64 = reinterpret_cast<int64_t *>(smem);
 
     const int64_t t0 = (int64_t)blockIdx.x * kBxT;
     const int64_t tbase = t0 - 1;
     const int d0 = blockIdx.y * kBxIn;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Staged index i is sample tbase + i; samples exist for i in [i_lo, i_hi).
+    const int i_lo = tbase < 0 ? (int)(-tbase) : 0;
+    const int i_hi = (int)min((int64_t)LP, n_out - tbase);
+    const int fit_end = (int)min(n_out - tbase, (int64_t)INT32_MAX);  // windows end by this index
 
-    // Phase 1: exclusive prefix sums P[r][i] = sum_{j<i} x(tbase + j).
+    // Phase 1 in 32-bit wrap-around prefix sums, tracking the value range.
+    // x = S - w*m0 is exact if maxw * max|v - m0| < 2^31 for every block
+    // whose windows start in this tile; otherwise redo it in 64 bits.
+    bool wide = false;
     for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
         const int d = d0 - 1 + rr;
-        const bool rv = d >= 0 && d < ndm;
+        if (d < 0 || d >= ndm) continue;
         const int32_t *row = dmt + (int64_t)d * n_out;
-        int64_t *Pr = P + (size_t)rr * (LP + 1);
-        if (lane == 0) Pr[0] = 0;
-        int64_t carry = 0;
-        for (int base = 0; base < LP; base += 32) {
-            const int i = base + lane;
-            const int64_t t = tbase + i;
-            int64_t v = (rv && i < LP && t >= 0 && t < n_out) ? (int64_t)__ldg(row + t) : 0;
+        int32_t vmin = INT32_MAX, vmax = INT32_MIN;
+        prefix_row<uint32_t>(row, tbase, LP, i_lo, i_hi, P32 + (size_t)rr * (LP + 1), vmin, vmax);
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += u;
-            }
-            if (i < LP) Pr[i + 1] = carry + v;
-            carry += __shfl_sync(0xffffffffu, v, 31);
+        for (int o = 16; o > 0; o >>= 1) {
+            vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+            vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        }
+        if (vmin > vmax) continue;
+        const int64_t ts = tbase + i_lo, te = tbase + min(i_hi, kBxTT) - 1;
+        int64_t bs = (norm_block > 0) ? ts / norm_block : 0, be = (norm_block > 0) ? te / norm_block : 0;
+        bs = min(bs, nblk - 1);
+        be = min(be, nblk - 1);
+        for (int64_t b = bs + lane; b <= be; b += 32) {
+            const int64_t m0 = __ldg(m0s + (int64_t)d * nblk + b);
+            const int64_t dev = max((int64_t)vmax - m0, m0 - (int64_t)vmin);
+            if (dev * maxw > (int64_t)INT32_MAX) wide = true;
+        }
+    }
+    wide = __syncthreads_or(wide);
+    if (wide) {
+        for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
+            const int d = d0 - 1 + rr;
+            if (d < 0 || d >= ndm) continue;
+            int32_t vmin = 0, vmax = 0;
+            prefix_row<int64_t>(dmt + (int64_t)d * n_out, tbase, LP, i_lo, i_hi, P64 + (size_t)rr * (LP + 1),
+                                vmin, vmax);
         }
     }
     __syncthreads();
@@ -135,64 +274,34 @@ sps_boxcar_kernel(const int32_t *__restrict__ dmt, int32_t ndm, int64_t n_out, W
     // Phase 2: best S/N over the widths for every staged (row, sample).
     for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
         const int d = d0 - 1 + rr;
-        const bool rv = d >= 0 && d < ndm;
-        const int64_t *Pr = P + (size_t)rr * (LP + 1);
-        int64_t cb = -1;
-        int64_t m0 = 0;
-        float2 cf[SP_MAX_WIDTHS];
-#pragma unroll
-        for (int k = 0; k < SP_MAX_WIDTHS; ++k) cf[k] = make_float2(0.f, 0.f);
-        for (int j = 0; j < kBxPerLane; ++j) {
-            const int ti = lane * kBxPerLane + j;
-            if (ti >= kBxTT) break;
-            const int64_t t = tbase + ti;
-            float best = -INFINITY;
-            int kb = -1;
-            if (rv && t >= 0 && t < n_out) {
-                int64_t b = (norm_block > 0) ? t / norm_block : 0;
-                if (b > nblk - 1) b = nblk - 1;
-                if (b != cb) {
-                    cb = b;
-                    const int64_t idx = (int64_t)d * nblk + b;
-                    m0 = __ldg(m0s + idx);
-#pragma unroll
-                    for (int k = 0; k < SP_MAX_WIDTHS; ++k)
-                        if (k < wl.nw) cf[k] = __ldg(coefs + idx * wl.nw + k);
-                }
-                const int64_t p0 = Pr[ti];
-#pragma unroll
-                for (int k = 0; k < SP_MAX_WIDTHS; ++k) {
-                    if (k < wl.nw) {
-                        const int w = wl.w[k];
-                        if (t + w <= n_out) {
-                            const int64_t x = Pr[ti + w] - p0 - (int64_t)w * m0;
-                            const float s = fmaf((float)x, cf[k].x, -cf[k].y);
-                            if (kb < 0 || s > best) {
-                                best = s;
-                                kb = k;
-                            }
-                        }
-                    }
-                }
-            }
-            snr_s[rr * kBxTT + ti] = best;
-            k_s[rr * kBxTT + ti] = (int8_t)kb;
+        if (d < 0 || d >= ndm) {
+            for (int ti = lane; ti < kBxTT; ti += 32) snr_s[rr * kBxTT + ti] = -INFINITY;
+            continue;
         }
+        if (wide)
+            score_row<int64_t>(P64 + (size_t)rr * (LP + 1), d, tbase, i_lo, i_hi, fit_end, wl, norm_block, nblk,
+                               m0s, coefs, snr_s + rr * kBxTT, k_s + rr * kBxTT);
+        else
+            score_row<uint32_t>(P32 + (size_t)rr * (LP + 1), d, tbase, i_lo, i_hi, fit_end, wl, norm_block,
+                                nblk, m0s, coefs, snr_s + rr * kBxTT, k_s + rr * kBxTT);
     }
     __syncthreads();
 
     // Phase 3: interior points -- map output, or threshold + 3x3 + append.
+    const int rows_in = min(kBxIn, ndm - d0);
+    const int t_in = (int)min((int64_t)kBxT, n_out - t0);
     for (int idx = threadIdx.x; idx < kBxIn * kBxT; idx += 256) {
-        const int rr = 1 + idx / kBxT;
-        const int ti = 1 + idx % kBxT;
-        const int d = d0 - 1 + rr;
-        const int64_t t = tbase + ti;
-        const bool inr = d < ndm && t < n_out;
+        const int r = idx / kBxT;
+        const int tt = idx % kBxT;
+        const int rr = 1 + r;
+        const int ti = 1 + tt;
+        const bool inr = r < rows_in && tt < t_in;
         const float v = snr_s[rr * kBxTT + ti];
         if (MAP) {
             if (inr) {
-                map_best[(int64_t)d * n_out + t] = v;
-                map_k[(int64_t)d * n_out + t] = k_s[rr * kBxTT + ti];
+                const int64_t o = (int64_t)(d0 + r) * n_out + t0 + tt;
+                map_best[o] = v;
+                map_k[o] = k_s[rr * kBxTT + ti];
             }
         } else {
             bool cand = inr && v >= thr;
@@ -213,8 +322,8 @@ sps_boxcar_kernel(const int32_t *__restrict__ dmt, int32_t ndm, int64_t n_out, W
                     const unsigned long long pos = base + __popc(mask & ((1u << lane) - 1u));
                     if ((int64_t)pos < cap) {
                         sp_cand c;
-                        c.dm_idx = d;
-                        c.t = (int32_t)t;
+                        c.dm_idx = d0 + r;
+                        c.t = (int32_t)(t0 + tt);
                         c.width_idx = k_s[rr * kBxTT + ti];
                         c.snr = v;
                         cands[pos] = c;

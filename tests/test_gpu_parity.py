@@ -117,6 +117,7 @@ SPS_CASES = [
     (20, 513, [1], 0, "flat"),                              # zero variance
     (1, 1, [1], 0, "noise"),
     (29, 2600, list(range(1, 17)), 500, "noise"),           # 16 widths
+    (10, 1000, [1, 4, 64, 256], 300, "huge"),               # |window sums| >= 2^31: 64-bit path
 ]
 
 
@@ -125,6 +126,8 @@ def _dmt_values(kind, ndm, n_out, rng):
         return np.rint(rng.normal(5.2e5, 1024.0, size=(ndm, n_out))).astype(np.int32)
     if kind == "signed":
         return rng.integers(-50000, 50000, size=(ndm, n_out)).astype(np.int32)
+    if kind == "huge":
+        return rng.integers(-10_000_000, 10_000_000, size=(ndm, n_out)).astype(np.int32)
     return np.full((ndm, n_out), 777, np.int32)
 
 

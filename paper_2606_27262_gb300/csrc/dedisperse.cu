@@ -12,13 +12,15 @@
 //                       from the plan) x 512 output samples.  Channels go in
 //                       chunks of 8: per channel the CTA stages the window of
 //                       input samples the tile's delays reach (512 + delay
-//                       spread + alignment slack).  Warp 0 fetches chunk k+1
-//                       with bulk asynchronous copies (TMA) while the CTA
-//                       sums chunk k; each warp then expands one channel of
-//                       the fetched chunk into four copies shifted by 0..3
-//                       bytes, so that any 4 consecutive samples are one
-//                       aligned 32-bit load.  One staged byte serves up to 32
-//                       DMs.
+//                       spread + alignment slack).  Warp 0 fetches chunk k+2
+//                       with bulk asynchronous copies (TMA) into a ring of
+//                       three raw slots while the CTA sums chunk k, so every
+//                       fetch has two chunks of work to land in; each warp
+//                       expands one channel of chunk k+1 into four copies
+//                       shifted by 0..3 bytes (double-buffered), so that any
+//                       4 consecutive samples are one aligned 32-bit load.
+//                       One barrier per chunk.  One staged byte serves up to
+//                       32 DMs.
 //
 // Arithmetic: the sum is a pure integer add of bytes (no tensor-core
 // contraction exists here).  Each thread owns 4 DMs x 16 samples.  For every
@@ -121,24 +123,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// Shared-memory layout (bytes):
-//   [0, 16)                    two mbarriers, one per staging buffer
-//   [16, 16 + 2*CH*16)         geometry of two chunks (window start, R, copies offset)
-//   [512, 512 + 2*CH*DT*4)     offset tables of two chunks
-//   then copies[2][copies_max] per channel four copies of stride S = R + 16:
-//                              copy r, word j = staged bytes [4j + r, 4j + r + 4).
-//                              Copy 0 is the staged row itself (written by TMA).
-//
-// Pipeline per CTA, one CTA barrier per chunk.  Iteration k:
-//   1. warp 0 issues the bulk copies of chunk k+1 (rows into the copy-0 slots
-//      of buffer (k+1) & 1, plus its offset table) on mbarrier (k+1) & 1 and
-//      publishes the geometry of chunk k+2;
-//   2. every warp sums chunk k from buffer k & 1;
-//   3. every warp waits for chunk k+1's bytes and derives copies 1..3 of its
-//      channel from copy 0;
-//   4. barrier (also the point where a staging time-out is agreed on).
-// A buffer is refilled only after the barrier that follows its last reader.
-//
 // Summation: for four channels a..d of a chunk and one trial DM, each thread
 // loads one aligned word per channel (4 consecutive samples, from the copy
 // that matches the channel's delay modulo 4), transposes the 4x4 bytes with
@@ -154,24 +138,41 @@ __device__ __forceinline__ void add_quad(uint32_t wa, uint32_t wb, uint32_t wc, 
     acc[3] = (int32_t)__dp4a(__byte_perm(t1, t3, 0x7632), 0x01010101u, (uint32_t)acc[3]);
 }
 
+// Shared-memory layout (bytes):
+//   [0, 8*NS)                 one mbarrier per raw slot
+//   [64, 64 + NS*CH*16)       geometry of the chunk in each raw slot
+//   [512, 512 + NS*CH*DT*4)   offset table of the chunk in each raw slot
+//   then raw[NS][raw_max]     raw channel rows as copied from global memory
+//   then copies[2][copies_max] per channel four copies of stride R:
+//                             copy r, word j = staged bytes [4j + r, 4j + r + 4)
+//
+// Iteration k: warp 0 issues chunk k+2 into raw slot (k+2) % NS; every warp
+// sums chunk k from copies buffer k & 1, then waits for chunk k+1's bytes and
+// expands its channel of it into copies buffer (k+1) & 1; barrier.  A raw
+// slot is refilled two barriers after its chunk was expanded; a copies
+// buffer one barrier after its chunk was summed.
 template <int NDT, int NWARP, int CH>
 __global__ void __launch_bounds__(NWARP * 32, 2)
 dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, int32_t nchunks,
                   const int32_t *__restrict__ tile_first, const int32_t *__restrict__ tile_count,
                   const int4 *__restrict__ chunk_geo, const int32_t *__restrict__ chunk_off, int32_t copies_max,
-                  int64_t n_out, int32_t *__restrict__ out, int32_t *__restrict__ status) {
+                  int32_t raw_max, int64_t n_out, int32_t *__restrict__ out, int32_t *__restrict__ status) {
     static_assert(NDT == 4, "offset table is read as int4 per thread");
     constexpr int DT = NDT * NWARP;
     constexpr int T = kDedispTimeTile;
+    constexpr int NS = kDedispRawSlots;
     static_assert(T == 32 * 16, "a warp spans the time tile: 32 lanes x 16 samples");
     static_assert(CH <= 31 && NWARP == CH && CH % 4 == 0, "warp 0 lanes issue one channel each; one warp per channel");
     static_assert(DT == kDedispDmTile && CH == kDedispChanChunk, "layout shared with the plan");
+    static_assert(8 * NS <= kDedispGeoOffset, "mbarriers overlap the geometry ring");
+    static_assert(kDedispGeoOffset + NS * CH * 16 <= kDedispOffTabOffset, "geometry ring overlaps the offsets");
 
     extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
-    int4 *geo_s = reinterpret_cast<int4 *>(smem + kDedispGeoOffset);           // [2][CH]
-    int32_t *offt_s = reinterpret_cast<int32_t *>(smem + kDedispOffTabOffset);  // [2][CH*DT]
-    uint8_t *cop_s = smem + kDedispHeaderBytes;                                 // [2][copies_max]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);                       // [NS]
+    int4 *geo_s = reinterpret_cast<int4 *>(smem + kDedispGeoOffset);           // [NS][CH]
+    int32_t *offt_s = reinterpret_cast<int32_t *>(smem + kDedispOffTabOffset);  // [NS][CH*DT]
+    uint8_t *raw_s = smem + kDedispHeaderBytes;                                 // [NS][raw_max]
+    uint8_t *cop_s = raw_s + NS * raw_max;                                      // [2][copies_max]
 
     const int tile = blockIdx.x;
     const int64_t t0 = (int64_t)blockIdx.y * T;
@@ -184,47 +185,48 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
     const int32_t *off_g = chunk_off + (int64_t)tile * nchunks * CH * DT;
     const int4 zero4 = make_int4(0, 0, 0, 0);
 
-    if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        fence_mbar_init();
-    }
+    if (threadIdx.x < NS) mbar_init(&mbar[threadIdx.x], 1);
+    if (threadIdx.x == 0) fence_mbar_init();
     __syncthreads();
 
-    // Warp 0: bulk copies of chunk kk (g = the lane's channel geometry).
-    auto issue = [&](int kk, int4 g) {
-        const int b = kk & 1;
+    auto issue = [&](int kk, int4 g) {  // warp 0; chunk kk into raw slot kk % NS
+        const int sl = kk % NS;
         const int nc = min(CH, nchan - kk * CH);
         uint32_t bytes = (lane < nc) ? (uint32_t)g.y + 16u : 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+        if (lane < CH) geo_s[sl * CH + lane] = (lane < nc) ? g : zero4;
         fence_proxy_async();
-        if (lane == 0) mbar_arrive_expect_tx(&mbar[b], bytes + (uint32_t)(CH * DT * 4));
+        if (lane == 0) mbar_arrive_expect_tx(&mbar[sl], bytes + (uint32_t)(CH * DT * 4));
         __syncwarp();
         if (lane < nc)
-            bulk_g2s(cop_s + b * copies_max + g.z, xt + (int64_t)(kk * CH + lane) * pitch + t0 + g.x,
-                     (uint32_t)g.y + 16u, &mbar[b]);
-        if (lane == CH) bulk_g2s(offt_s + b * CH * DT, off_g + (int64_t)kk * CH * DT, CH * DT * 4, &mbar[b]);
+            bulk_g2s(raw_s + sl * raw_max + g.w, xt + (int64_t)(kk * CH + lane) * pitch + t0 + g.x,
+                     (uint32_t)g.y + 16u, &mbar[sl]);
+        if (lane == CH) bulk_g2s(offt_s + sl * CH * DT, off_g + (int64_t)kk * CH * DT, CH * DT * 4, &mbar[sl]);
     };
     auto load_geo = [&](int kk) -> int4 {
         return (kk < nchunks && lane < CH && kk * CH + lane < nchan) ? __ldg(geo_g + (int64_t)kk * CH + lane)
                                                                       : zero4;
     };
-    // Derive copies 1..3 of this warp's channel of chunk kk (buffer b) from copy 0.
-    auto build = [&](int kk, int b) {
+    // Four shifted copies of this warp's channel of chunk kk, from raw slot
+    // kk % NS into copies buffer kk & 1.
+    auto build = [&](int kk) {
+        const int sl = kk % NS;
         if (kk * CH + warp >= nchan) return;
-        const int4 g = geo_s[b * CH + warp];
-        const int32_t R = g.y, S = g.y + 16;
-        uint8_t *row = cop_s + b * copies_max + g.z;
+        const int4 g = geo_s[sl * CH + warp];
+        const int32_t R = g.y, S = g.y;
+        const uint8_t *src = raw_s + sl * raw_max + g.w;
+        uint8_t *row = cop_s + (kk & 1) * copies_max + g.z;
         const int nseg = R / 16;
         for (int q0 = 0; q0 < nseg; q0 += 32) {
             const int q = q0 + lane;
             const bool act = q < nseg;
             uint4 a = make_uint4(0u, 0u, 0u, 0u);
-            if (act) a = *reinterpret_cast<const uint4 *>(row + 16 * q);
+            if (act) a = *reinterpret_cast<const uint4 *>(src + 16 * q);
             uint32_t e = __shfl_down_sync(0xffffffffu, a.x, 1);
-            if (act && (lane == 31 || q + 1 >= nseg)) e = *reinterpret_cast<const uint32_t *>(row + 16 * q + 16);
+            if (act && (lane == 31 || q + 1 >= nseg)) e = *reinterpret_cast<const uint32_t *>(src + 16 * q + 16);
             if (act) {
+                *reinterpret_cast<uint4 *>(row + 16 * q) = a;
                 *reinterpret_cast<uint4 *>(row + S + 16 * q) =
                     make_uint4(__byte_perm(a.x, a.y, 0x4321), __byte_perm(a.y, a.z, 0x4321),
                                __byte_perm(a.z, a.w, 0x4321), __byte_perm(a.w, e, 0x4321));
@@ -238,22 +240,17 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
         }
     };
 
-    // Prologue: stage chunk 0 and derive its copies; publish chunk 1's geometry.
-    int4 g_k1 = zero4, g_k2 = zero4;
+    int4 g_next = zero4;  // warp 0: geometry of the next chunk to issue
     if (warp == 0) {
-        const int4 g0 = load_geo(0);
-        g_k1 = load_geo(1);
-        g_k2 = load_geo(2);
-        if (lane < CH) {
-            geo_s[lane] = g0;
-            geo_s[CH + lane] = g_k1;
-        }
+        const int4 g0 = load_geo(0), g1 = load_geo(1);
+        g_next = load_geo(2);
         issue(0, g0);
+        if (nchunks > 1) issue(1, g1);
     }
     __syncthreads();
     {
         const bool ok = mbar_wait_bounded(&mbar[0], 0u);
-        if (ok) build(0, 0);
+        if (ok) build(0);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicOr(status, SP_STATUS_STAGING_TIMEOUT);
             return;
@@ -269,16 +266,13 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
     for (int k = 0; k < nchunks; ++k) {
         const int b = k & 1;
         const int nc = min(CH, nchan - k * CH);
-        if (warp == 0 && k + 1 < nchunks) {
-            issue(k + 1, g_k1);
-            if (lane < CH) geo_s[b * CH + lane] = g_k2;  // chunk k+2 lives in buffer b
-            g_k1 = g_k2;
-            g_k2 = load_geo(k + 3);
+        if (warp == 0 && k + 2 < nchunks) {
+            issue(k + 2, g_next);
+            g_next = load_geo(k + 3);
         }
-
         if (warp_active) {
             const uint8_t *sb = cop_s + b * copies_max + lane * 4;
-            const int32_t *ot = offt_s + b * CH * DT + warp * NDT;
+            const int32_t *ot = offt_s + (k % NS) * CH * DT + warp * NDT;
             if (nc == CH) {
 #pragma unroll
                 for (int qd = 0; qd < CH / 4; ++qd) {
@@ -301,7 +295,6 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
                     }
                 }
             } else {
-                // Last, partial chunk: one channel at a time.
                 for (int c = 0; c < nc; ++c) {
                     const int4 oc = *reinterpret_cast<const int4 *>(ot + c * DT);
                     const int32_t ac[4] = {oc.x, oc.y, oc.z, oc.w};
@@ -316,11 +309,10 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
                 }
             }
         }
-
         bool ok = true;
         if (k + 1 < nchunks) {
-            ok = mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
-            if (ok) build(k + 1, b ^ 1);
+            ok = mbar_wait_bounded(&mbar[(k + 1) % NS], (uint32_t)((k + 1) / NS) & 1u);
+            if (ok) build(k + 1);
         }
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicOr(status, SP_STATUS_STAGING_TIMEOUT);
@@ -350,8 +342,10 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
 }
 
 using DedispKernel = void (*)(const uint8_t *, int64_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                              const int4 *, const int32_t *, int32_t, int64_t, int32_t *, int32_t *);
+                              const int4 *, const int32_t *, int32_t, int32_t, int64_t, int32_t *, int32_t *);
 constexpr DedispKernel kDedisp = dedisperse_kernel<kDedispDmPerThread, kDedispWarps, kDedispChanChunk>;
+
+
 
 }  // namespace
 
@@ -376,7 +370,7 @@ int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, i
     const dim3 grid((unsigned)plan->ntiles, (unsigned)ntime);
     kDedisp<<<grid, kDedispWarps * 32, plan->smem_bytes, stream>>>(
         d_xt, pitch, plan->nchan, plan->nchunks, plan->d_tile_first, plan->d_tile_count, plan->d_chunk_geo,
-        plan->d_chunk_off, plan->copies_max, n_out, d_out, plan->d_status);
+        plan->d_chunk_off, plan->copies_max, plan->raw_max, n_out, d_out, plan->d_status);
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

@@ -51,22 +51,22 @@ int compute_delays(const double *freqs, int32_t nchan, double tsamp, const doubl
 // Time tiles start at multiples of kDedispTimeTile (a multiple of 16), so the
 // 16-byte-aligned window start of a channel relative to the time tile is
 // (min delay over the tile) rounded down to 16 and does not depend on the
-// time tile; neither do the offsets derived from it.  Each channel's four
-// byte-shifted copies have stride R + 16: copy 0 is the staged row itself,
-// 16 bytes longer than the R bytes any copy is read over, so that copies
-// 1..3 can be derived from it.
+// time tile; neither do the offsets derived from it.  A channel occupies
+// R + 16 bytes of a raw staging slot (the window plus the 16 bytes its
+// shifted copies reach past it) and 4 R bytes of a copies buffer (its four
+// byte-shifted copies, stride R).
 void build_chunk_tables(const sp_plan &p, std::vector<int32_t> &geo, std::vector<int32_t> &off,
-                        int32_t *copies_max) {
+                        int32_t *copies_max, int32_t *raw_max) {
     const int32_t CH = kDedispChanChunk, DT = kDedispDmTile;
     geo.assign((size_t)p.ntiles * p.nchunks * CH * 4, 0);
     off.assign((size_t)p.ntiles * p.nchunks * CH * DT, 0);
-    int32_t cmax = 0;
+    int32_t cmax = 0, rmax = 0;
     for (int32_t j = 0; j < p.ntiles; ++j) {
         const int32_t d0 = p.tile_first[j], cnt = p.tile_count[j];
         for (int32_t k = 0; k < p.nchunks; ++k) {
             const int32_t c0 = k * CH;
             const int32_t nc = std::min(CH, p.nchan - c0);
-            int32_t soff = 0;
+            int32_t soff = 0, roff = 0;
             for (int32_t i = 0; i < nc; ++i) {
                 const int32_t c = c0 + i;
                 int32_t lo = INT32_MAX, hi = 0;
@@ -77,12 +77,12 @@ void build_chunk_tables(const sp_plan &p, std::vector<int32_t> &geo, std::vector
                 }
                 const int32_t rel_base = lo & ~15;
                 const int32_t R = dedisp_row_bytes(hi - lo);
-                const int32_t stride = R + 16;
+                const int32_t stride = R;  // copies are derived from the raw slot: no tail needed
                 int32_t *g = &geo[(((size_t)j * p.nchunks + k) * CH + i) * 4];
                 g[0] = rel_base;
                 g[1] = R;
                 g[2] = soff;
-                g[3] = 0;
+                g[3] = roff;
                 int32_t *o = &off[(((size_t)j * p.nchunks + k) * CH + i) * DT];
                 for (int32_t dl = 0; dl < DT; ++dl) {
                     const int32_t dd = std::min(dl, cnt - 1);  // idle slots repeat the last DM
@@ -90,11 +90,14 @@ void build_chunk_tables(const sp_plan &p, std::vector<int32_t> &geo, std::vector
                     o[dl] = soff + (shift & 3) * stride + (shift & ~3);
                 }
                 soff += 4 * stride;
+                roff += R + 16;
             }
             cmax = std::max(cmax, soff);
+            rmax = std::max(rmax, roff);
         }
     }
     *copies_max = cmax;
+    *raw_max = rmax;
 }
 
 }  // namespace sp
@@ -169,8 +172,8 @@ extern "C" int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsa
     p->ntiles = (int32_t)p->tile_first.size();
     p->nchunks = (nchan + kDedispChanChunk - 1) / kDedispChanChunk;
     std::vector<int32_t> geo, off;
-    build_chunk_tables(*p, geo, off, &p->copies_max);
-    p->smem_bytes = kDedispHeaderBytes + 2 * p->copies_max;
+    build_chunk_tables(*p, geo, off, &p->copies_max, &p->raw_max);
+    p->smem_bytes = kDedispHeaderBytes + kDedispRawSlots * p->raw_max + 2 * p->copies_max;
 
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         cudaGetLastError();

@@ -18,12 +18,14 @@ constexpr int kDedispDmTile = kDedispDmPerThread * kDedispWarps;  // 32 DMs per 
 constexpr int kDedispTimeTile = 512;                      // output samples per CTA
 constexpr int kDedispChanChunk = 8;                       // channels staged per pass
 constexpr int kDedispMaxSpan = 1024;                      // max delay spread in a DM tile
-// Shared-memory header of the dedispersion kernel: two mbarriers, the
-// geometry of two chunks, and two (channel, DM) offset tables.
-constexpr int kDedispGeoOffset = 16;
+// Shared-memory header of the dedispersion kernel: one mbarrier per raw
+// staging slot, then per slot the geometry and the (channel, DM) offset table
+// of the chunk it holds.
+constexpr int kDedispGeoOffset = 64;
 constexpr int kDedispOffTabOffset = 512;
 constexpr int kDedispOffTabInts = kDedispChanChunk * kDedispDmTile;
-constexpr int kDedispHeaderBytes = kDedispOffTabOffset + 2 * kDedispOffTabInts * 4;
+constexpr int kDedispRawSlots = 3;                        // raw chunks in flight (two ahead)
+constexpr int kDedispHeaderBytes = kDedispOffTabOffset + kDedispRawSlots * kDedispOffTabInts * 4;
 // Staged-input row pitch: room for the last time tile's window past n_in,
 // rounded to 64 bytes.
 __host__ __device__ inline int64_t dedisp_pitch(int64_t n_in) {
@@ -49,6 +51,7 @@ struct sp_plan {
     int32_t nchunks = 0;          // channel chunks of kDedispChanChunk
     std::vector<int32_t> tile_first, tile_count;
     int32_t copies_max = 0;       // largest shifted-copy staging of one chunk (bytes)
+    int32_t raw_max = 0;          // largest raw staging of one chunk (bytes)
     int32_t smem_bytes = 0;       // dynamic shared memory of the dedispersion kernel
     // device copies
     int32_t *d_delays = nullptr;      // [ndm][nchan]
@@ -76,7 +79,7 @@ int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, i
                       int32_t *d_out, cudaStream_t stream);
 // Host-side layout of the per-(tile, chunk) staging tables (plan.cpp).
 void build_chunk_tables(const sp_plan &p, std::vector<int32_t> &geo, std::vector<int32_t> &off,
-                        int32_t *copies_max);
+                        int32_t *copies_max, int32_t *raw_max);
 
 struct SpsArgs {
     const int32_t *dmt;

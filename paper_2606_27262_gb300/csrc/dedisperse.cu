@@ -174,8 +174,21 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
     uint8_t *raw_s = smem + kDedispHeaderBytes;                                 // [NS][raw_max]
     uint8_t *cop_s = raw_s + NS * raw_max;                                      // [2][copies_max]
 
-    const int tile = blockIdx.x;
-    const int64_t t0 = (int64_t)blockIdx.y * T;
+    // Raster: groups of kDedispTileGroup DM tiles sweep all time tiles, so
+    // the CTAs resident at one time share an input window that fits in L2
+    // (DM-tile-fastest order would make them span the whole sweep).
+    int tile;
+    int64_t t0;
+    {
+        const int ntiles = gridDim.x, ntime = gridDim.y;
+        const int64_t id = (int64_t)blockIdx.y * ntiles + blockIdx.x;
+        const int64_t per_group = (int64_t)kDedispTileGroup * ntime;
+        const int group = (int)(id / per_group);
+        const int64_t r = id - group * per_group;
+        const int width = min(kDedispTileGroup, ntiles - group * kDedispTileGroup);
+        tile = group * kDedispTileGroup + (int)(r % width);
+        t0 = (r / width) * T;
+    }
     const int d_first = tile_first[tile];
     const int d_cnt = tile_count[tile];
     const int warp = threadIdx.x >> 5;

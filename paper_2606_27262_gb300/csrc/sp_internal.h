@@ -18,6 +18,7 @@ constexpr int kDedispDmTile = kDedispDmPerThread * kDedispWarps;  // 32 DMs per 
 constexpr int kDedispTimeTile = 512;                      // output samples per CTA
 constexpr int kDedispChanChunk = 8;                       // channels staged per pass
 constexpr int kDedispMaxSpan = 1024;                      // max delay spread in a DM tile
+constexpr int kDedispTileGroup = 24;                      // DM tiles per raster group
 // Shared-memory header of the dedispersion kernel: one mbarrier per raw
 // staging slot, then per slot the geometry and the (channel, DM) offset table
 // of the chunk it holds.

@@ -24,6 +24,13 @@ sample of the same workload on the host cores.
 Multi-GPU (torchrun): every rank searches its own beam (replicas, weak
 scaling, no collective on the data path); the timed region is bracketed by
 barriers and the slowest rank's time is reported.
+
+`--workload batched` measures the multi-beam step instead: 128 beams of
+4096 channels with lengths U{16384..131072} and max DM from {500, 1000,
+2000} (bandpass gains U(0.5, 1.5)), dedispersed in grouped persistent
+launches with the autotuned kernel shape and searched on a second stream,
+the whole step replayed as one CUDA graph; value = seconds of data searched
+per second, next to the same work as per-beam launches (also a graph).
 """
 from __future__ import annotations
 
@@ -60,6 +67,13 @@ def parse_args(argv=None):
     p.add_argument("--n-out", type=int, default=None,
                    help="searched samples per beam (default: the full 131072); smaller values are for "
                         "profiler captures only")
+    p.add_argument("--workload", choices=["single", "batched"], default="single")
+    p.add_argument("--beams", type=int, default=128, help="batched workload: number of beams")
+    p.add_argument("--dmt-budget-gb", type=float, default=24.0,
+                   help="batched workload: DM-transform bytes per group arena (GB)")
+    p.add_argument("--no-per-beam", action="store_true", help="batched workload: skip the comparisons")
+    p.add_argument("--batch-mode", choices=["persistent", "grid"], default="persistent",
+                   help="batched workload: dedispersion launch style of the timed step")
     return p.parse_args(argv)
 
 
@@ -318,6 +332,136 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- batched --
+def run_batched(args):
+    import numpy as np
+    import torch
+
+    import paper_2606_27262_gb300 as sp
+    import synth
+    from paper_2606_27262_gb300 import build as spbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    spbuild.build()
+    bw = synth.config3(nbeams=args.beams)
+    stream = torch.cuda.Stream(device=dev)  # graph capture needs a stream other than the legacy default
+    best, tune_ms = sp.autotune_dedisperse(bw.freqs, bw.tsamp, bw.plan_dms[-1], stream=stream)
+    plans = [sp.Plan(bw.freqs, bw.tsamp, d, shape=best) for d in bw.plan_dms]
+    cap = 1 << 19
+    batch = sp.Batch(plans, bw.beam_plan, bw.n_out, bw.widths, bw.threshold, bw.norm_block, cap,
+                     int(args.dmt_budget_gb * (1 << 30)))
+    for b in range(bw.nbeams):
+        synth.make_beam_torch(bw.beam_seed(b) + 7919 * rank, batch.input_tensor(b, bw.nchan), bw.freqs,
+                              bw.bursts(b), widths=bw.widths, gains=bw.gains(b))
+    torch.cuda.synchronize(dev)
+    ndms = np.array([plans[p].ndm for p in bw.beam_plan], np.float64)
+    adds = float(np.sum(ndms * bw.n_out.astype(np.float64))) * bw.nchan
+    data_s = float(np.sum(bw.n_out)) * bw.tsamp
+
+    # Dedispersion kernel time inside a grouped step (events around each
+    # group's persistent launch on the launching stream), for the roofline.
+    batch.run({"persistent": sp.SP_BATCH_GROUPED, "grid": sp.SP_BATCH_GROUPED_GRID}[args.batch_mode]
+              | sp.SP_BATCH_TIMED, stream)
+    torch.cuda.synchronize(dev)
+    group_ms = batch.group_ms()
+    lanes, nsm = sp.probe_iadd3_rate()
+
+    def timed_graph(mode, steps, warmup):
+        batch.capture(mode, stream)
+        for _ in range(max(warmup, 0)):
+            batch.launch(stream)
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for k in range(steps):
+            batch.launch(stream)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        return reduce_max(ev[0].elapsed_time(ev[-1]), world, dev) / steps
+
+    main_mode = {"persistent": sp.SP_BATCH_GROUPED, "grid": sp.SP_BATCH_GROUPED_GRID}[args.batch_mode]
+    per_beam, other = None, None
+    if not args.no_per_beam:
+        pb_ms = timed_graph(sp.SP_BATCH_PER_BEAM, max(1, args.steps // 2), 1)
+        per_beam = {"value": world * data_s / (pb_ms / 1e3), "unit": "beams", "ms_per_step": pb_ms,
+                    "launches": "per beam: stage, dedisperse (grid kernel), statistics, boxcar; one stream; "
+                                "captured as one CUDA graph"}
+        alt = sp.SP_BATCH_GROUPED_GRID if main_mode == sp.SP_BATCH_GROUPED else sp.SP_BATCH_GROUPED
+        alt_ms = timed_graph(alt, max(1, args.steps // 2), 1)
+        other = {"mode": "grid" if alt == sp.SP_BATCH_GROUPED_GRID else "persistent",
+                 "value": world * data_s / (alt_ms / 1e3), "ms_per_step": alt_ms}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms_step = timed_graph(main_mode, args.steps, args.warmup)
+    clk = clocks.stop()
+    counts = [batch.count(b, stream) for b in range(bw.nbeams)]
+    value = world * data_s / (ms_step / 1e3)
+    dd_ms = float(np.sum(group_ms))
+    achieved = adds / (dd_ms / 1e3) / 1e12
+    peak = nsm * lanes * MAX_SM_MHZ * 1e6 / 1e12
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t_cpu, work = 0.0, 0.0
+        stride = 4 * args.cpu_stride
+        for p in range(len(bw.plan_dms)):
+            b = int(np.flatnonzero(bw.beam_plan == p)[0])
+            x = batch.input_tensor(b, bw.nchan).cpu().numpy()
+            rows = np.arange(0, bw.plan_dms[p].size, stride)
+            t0 = time.perf_counter()
+            dmt = oracle.dedisperse(x, oracle.delays(bw.freqs, bw.tsamp, bw.plan_dms[p][rows]), int(bw.n_out[b]))
+            oracle.best(dmt, bw.widths, bw.norm_block)
+            t_cpu += time.perf_counter() - t0
+            work += float(rows.size) * int(bw.n_out[b]) * bw.nchan
+        full_s = t_cpu * adds / work
+        cpu = {"value": data_s / full_s, "unit": "beams", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"oracle dedispersion + boxcar S/N on every {stride}th trial DM of one beam per DM "
+                         f"plan (full length), {t_cpu:.1f} s, scaled by channel x DM x sample count"}
+
+    ngroups = batch.ngroups
+    line = {
+        "metric": METRIC, "value": value, "unit": "beams", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded noise drawn on the device, per-channel gains, injected dispersed bursts)",
+        "config": {"workload": bw.name, "nbeams": bw.nbeams, "data_seconds": data_s,
+                   "shape": dict(zip(("dm_tile", "time_tile", "chan_chunk"), sp.shape_info(best))),
+                   "autotune_ms": [float(v) for v in tune_ms], "groups": ngroups,
+                   "dmt_budget_bytes": int(args.dmt_budget_gb * (1 << 30)), "device_bytes": batch.device_bytes,
+                   "graph": True, "widths": [int(w) for w in bw.widths], "threshold": bw.threshold,
+                   "norm_block": bw.norm_block,
+                   "l2": "inputs larger than L2 (0.1-0.7 GB per beam, 52 GB per batch), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "gchan_dm_samp_per_s": adds / (ms_step / 1e3) / 1e9,
+        "batch_mode": args.batch_mode, "other_batch_mode": other,
+        "per_beam": per_beam,
+        "speedup_vs_per_beam": (per_beam["ms_per_step"] / ms_step) if per_beam else None,
+        "candidates": int(sum(counts)),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "dedisperse_batch_kernel",
+                     "kernel_ms_per_step": dd_ms,
+                     "peak_basis": f"{nsm} SMs x {lanes:.1f} measured 32-bit add lanes/SM/clk x "
+                                   f"{MAX_SM_MHZ:.0f} MHz"},
+        "e2e": None, "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": (2 * bw.nbeams + bw.nbeams + ngroups) * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------- reference --
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -355,6 +499,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

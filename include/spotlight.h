@@ -17,8 +17,8 @@
  *     work is enqueued on it and the call returns without waiting, except
  *     where a call says it synchronises.  Buffers must stay valid until the
  *     stream has executed the work.
- *   - Only sp_plan_create and sp_searcher_create allocate device memory; the
- *     other calls allocate nothing.  Calls on different streams may overlap
+ *   - Only the plan, searcher and batch create calls and the autotuner
+ *     allocate device memory; the other calls allocate nothing.  Calls on different streams may overlap
  *     as long as they do not share output or workspace buffers.
  *   - Filterbank layout: uint8 [n_in][nchan], time-major (the order a
  *     filterbank file or ring block stores samples), channel 0 = the highest
@@ -98,6 +98,46 @@ int sp_plan_delays(const sp_plan *plan, int32_t *h_out);
 int sp_compute_delays(const double *freqs_mhz, int32_t nchan, double tsamp_s,
                       const double *dms, int32_t ndm, int32_t *h_out, int32_t *max_delay);
 
+/* ------------------------------------------- kernel shapes, autotuner --
+ * The dedispersion kernel is compiled for SP_DEDISP_NUM_SHAPES tile shapes,
+ * each a (DM tile, time tile, channel chunk) triple: shape 0 = 32 trial DMs
+ * x 512 samples x 8 channels (the shape of sp_plan_create), 1 = 32 x 256 x 8,
+ * 2 = 16 x 512 x 4.  A plan is built for one shape (its DM tiles and staging
+ * tables depend on it).  The shape changes speed only: every shape computes
+ * the same DM transform, bit for bit.  Choosing it by measurement has no
+ * counterpart in the paper (whose kernels come from its dedispersion
+ * library); it exists because the best tile shape depends on the channel
+ * count, the DM list and the GPU.
+ * sp_dedisp_shape_info: the triple of a shape (out pointers may be NULL).
+ * sp_plan_create_shaped: sp_plan_create for a given shape, or for
+ *   SP_SHAPE_AUTO: the shape sp_autotune_dedisperse picks with
+ *   SP_AUTOTUNE_SAMPLES searched samples and SP_AUTOTUNE_REPS repetitions.
+ * sp_plan_shape: the plan's shape, DM-tile count and the dedispersion
+ *   kernel's dynamic shared memory in bytes (out pointers may be NULL).
+ * sp_autotune_dedisperse: for each shape, builds a plan for (freqs, dms),
+ *   stages a synthetic input of n_out_sample searched samples
+ *   (n_in = n_out_sample + max_delay) and times `reps` launches of the
+ *   dedispersion kernel after one warm-up launch, with CUDA events on
+ *   `stream`; h_ms [SP_DEDISP_NUM_SHAPES] receives the mean milliseconds per
+ *   launch (+inf for a shape that cannot run this plan) and *best the
+ *   fastest shape.  Synchronous; allocates and frees temporary device
+ *   memory (n_in * nchan + ndm * n_out_sample * 4 bytes).  The result is
+ *   cached for the process per (device, inputs): a repeated call returns the
+ *   cached timings without launching anything.
+ * Errors: SP_EINVAL (bad shape or arguments, n_out_sample < 1, reps < 1),
+ *   the plan-creation errors, SP_ENOMEM, SP_ECUDA. */
+#define SP_DEDISP_NUM_SHAPES 3
+#define SP_SHAPE_AUTO (-1)
+#define SP_AUTOTUNE_SAMPLES 16384
+#define SP_AUTOTUNE_REPS 3
+int sp_dedisp_shape_info(int32_t shape, int32_t *dm_tile, int32_t *time_tile, int32_t *chan_chunk);
+int sp_plan_create_shaped(const double *freqs_mhz, int32_t nchan, double tsamp_s,
+                          const double *dms, int32_t ndm, int32_t shape, sp_plan **out);
+int sp_plan_shape(const sp_plan *plan, int32_t *shape, int32_t *ntiles, int32_t *smem_bytes);
+int sp_autotune_dedisperse(const double *freqs_mhz, int32_t nchan, double tsamp_s,
+                           const double *dms, int32_t ndm, int64_t n_out_sample, int32_t reps,
+                           float *h_ms, int32_t *best, void *stream);
+
 /* ----------------------------------------------------------- dedisperse --
  * Brute-force incoherent dedispersion (Sec. 3.1.1, the DM transform):
  *   d_out[d][t] = sum_{c < nchan} d_in[t + delay[d][c]][c],  0 <= t < n_out,
@@ -132,6 +172,39 @@ int sp_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_
                    int64_t pitch, void *stream);
 int sp_dedisperse_staged(const sp_plan *plan, const uint8_t *d_staged, int64_t pitch, int64_t n_in,
                          int32_t *d_out, int64_t n_out, void *stream);
+
+/* Many beams in one launch (the multi-beam operation of Sec. 2 and 3.1:
+ * every beam is searched independently; beams may differ in length, DM list
+ * and channel count).  One persistent kernel takes (beam, DM tile, time
+ * tile) items from a work queue until all beams are done; each beam's result
+ * is exactly that of sp_dedisperse_staged.
+ *   h_beams [nbeams]  host array, read during the call:
+ *     plan      the beam's plan; every plan must have the same shape and
+ *               belong to the current device;
+ *     d_staged  the staged beam (sp_stage_input), 256-byte aligned;
+ *     pitch     its row pitch, >= sp_staged_pitch(n_in), a multiple of 64;
+ *     n_in      input samples;
+ *     d_out     [plan ndm][n_out] int32 device, disjoint from the others;
+ *     n_out     must equal n_in - the plan's max delay (else SP_ESHAPE).
+ *   d_work / work_bytes  device scratch of at least
+ *     sp_dedisperse_batch_workspace_bytes(nbeams) bytes, 256-byte aligned
+ *     (the work queue and the beam table, copied there from host memory on
+ *     `stream`, so this call cannot be captured into a CUDA graph; the batch
+ *     object below can).
+ * A staging wait that runs out sets SP_STATUS_STAGING_TIMEOUT in the status
+ * word of h_beams[0].plan.
+ * Errors: SP_EINVAL, SP_ESHAPE, SP_EWORKSPACE, SP_ELIMIT, SP_ECUDA. */
+typedef struct {
+    const sp_plan *plan;
+    const uint8_t *d_staged;
+    int64_t pitch;
+    int64_t n_in;
+    int32_t *d_out;
+    int64_t n_out;
+} sp_batch_beam;
+int64_t sp_dedisperse_batch_workspace_bytes(int32_t nbeams);
+int sp_dedisperse_batch(const sp_batch_beam *h_beams, int32_t nbeams, void *d_work,
+                        int64_t work_bytes, void *stream);
 
 /* ------------------------------------------------- single-pulse search --
  * Boxcar matched-filter search of a DM transform (Sec. 3.1.2).
@@ -221,6 +294,83 @@ int sp_searcher_run(sp_searcher *s, const uint8_t *d_in, sp_cand *d_cands, int64
  * (after filling h_cands) when the total exceeds min(cap, cand_cap). */
 int sp_searcher_run_host(sp_searcher *s, const uint8_t *h_in, sp_cand *h_cands, int64_t cap,
                          int64_t *h_count, void *stream);
+
+/* ----------------------------------------------------------------- batch --
+ * A fixed set of beams searched as one step: the multi-beam workload of one
+ * GPU (Sec. 2: each GPU searches many beams in real time).  Beam b has plan
+ * plans[h_beam_plan[b]] and n_out = h_beam_n_out[b] searched samples
+ * (n_in = n_out + that plan's max delay); all beams share the width list,
+ * threshold, normalisation block and candidate capacity, and all plans must
+ * have the same shape (sp_plan_shape) and belong to the current device.
+ * The batch owns every device buffer of the step: each beam's input,
+ * staged inputs, DM transforms, search workspace, candidates and counts.
+ * DM transforms are not all held at once: beams are taken in order into
+ * groups whose transforms fit in dmt_budget_bytes (a beam larger than the
+ * budget forms a group alone), and two group arenas alternate.
+ *
+ * A run (mode SP_BATCH_GROUPED) does, per group: stage the group's beams,
+ * dedisperse all of them in one persistent launch (sp_dedisperse_batch),
+ * then search each beam (sp_single_pulse_search) on a second stream owned
+ * by the batch (at the device's highest stream priority), so that group
+ * g's search overlaps group g+1's dedispersion.  SP_BATCH_GROUPED_GRID is
+ * the same with one CTA per work item instead of a persistent grid, so that
+ * the block scheduler can run search CTAs between retiring dedispersion
+ * CTAs.  Mode SP_BATCH_PER_BEAM does the same work beam by beam on `stream`
+ * with one launch per step (stage, sp_dedisperse_staged, search): the
+ * comparison the batch exists to beat.  Every mode gives every beam the
+ * result its own sp_searcher would give.
+ *
+ * sp_batch_input: device pointer and n_in of beam b's input buffer (uint8
+ *   [n_in][nchan], time-major, 256-byte aligned), which the caller fills
+ *   before a run.
+ * sp_batch_run: enqueues one run on `stream` (asynchronous).  Adding
+ *   SP_BATCH_TIMED to a grouped mode also records CUDA events around each
+ *   group's persistent dedispersion launch on `stream`; sp_batch_group_ms
+ *   then waits for them and writes each group's launch time in ms to
+ *   h_ms [ngroups] (SP_EINVAL if the last run or capture was not timed).
+ * sp_batch_capture: records one run of `mode` on `stream` into a CUDA graph
+ *   held by the batch (replacing any earlier one); nothing executes.
+ *   sp_batch_launch enqueues that graph on `stream`.  Make the first run or
+ *   capture before any other capture is active on the device.
+ * sp_batch_results: after the run, waits for `stream` and copies beam b's
+ *   total count to *h_count and min(count, cap, cand_cap) candidates
+ *   (unspecified order) to h_cands; SP_EOVERFLOW (after copying) if the
+ *   count exceeds min(cap, cand_cap).
+ * sp_batch_dmt: beam b's DM transform [ndm][n_out] as left by the last run,
+ *   if the arenas still hold it (beams of the last two groups of a grouped
+ *   run, the last beam of a per-beam run); else SP_EINVAL.
+ * sp_batch_run_host: end to end from host memory: copies h_in[b] (n_in *
+ *   nchan bytes each; page-locked memory makes the copies asynchronous) into
+ *   the beams' inputs, runs SP_BATCH_GROUPED, then copies every beam's count
+ *   to h_counts [nbeams] and its first min(count, cap_per_beam, cand_cap)
+ *   candidates to h_cands + b * cap_per_beam.  Synchronises `stream`;
+ *   SP_EOVERFLOW (after copying) if any beam overflowed.
+ * sp_batch_status: OR of the status words of the batch and of its plans
+ *   (SP_STATUS_*), after synchronising the device; clear != 0 resets them.
+ * sp_batch_info: group count and total device bytes the batch holds.
+ * Errors: SP_EINVAL, SP_ESHAPE, SP_ELIMIT, SP_ENOMEM, SP_ECUDA. */
+typedef struct sp_batch sp_batch;
+#define SP_BATCH_GROUPED 0
+#define SP_BATCH_PER_BEAM 1
+#define SP_BATCH_GROUPED_GRID 2
+#define SP_BATCH_TIMED 16
+int sp_batch_create(const sp_plan *const *plans, int32_t nplans, const int32_t *h_beam_plan,
+                    const int64_t *h_beam_n_out, int32_t nbeams, const int32_t *h_widths,
+                    int32_t nw, float threshold, int64_t norm_block, int64_t cand_cap,
+                    int64_t dmt_budget_bytes, sp_batch **out);
+int sp_batch_destroy(sp_batch *b);
+int sp_batch_info(const sp_batch *b, int32_t *ngroups, int64_t *device_bytes);
+int sp_batch_input(sp_batch *b, int32_t beam, uint8_t **d_in, int64_t *n_in);
+int sp_batch_run(sp_batch *b, int32_t mode, void *stream);
+int sp_batch_group_ms(const sp_batch *b, float *h_ms);
+int sp_batch_capture(sp_batch *b, int32_t mode, void *stream);
+int sp_batch_launch(sp_batch *b, void *stream);
+int sp_batch_results(sp_batch *b, int32_t beam, sp_cand *h_cands, int64_t cap, int64_t *h_count,
+                     void *stream);
+int sp_batch_dmt(const sp_batch *b, int32_t beam, const int32_t **d_dmt);
+int sp_batch_run_host(sp_batch *b, const uint8_t *const *h_in, sp_cand *h_cands,
+                      int64_t cap_per_beam, int64_t *h_counts, void *stream);
+int sp_batch_status(const sp_batch *b, int32_t *h_status, int32_t clear);
 
 #ifdef __cplusplus
 }

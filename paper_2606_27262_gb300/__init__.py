@@ -13,6 +13,9 @@ Names mirror the C entry points:
 * ``single_pulse_search``        sp_single_pulse_search
 * ``best_snr_map``               sp_best_snr_map
 * ``Searcher``                   sp_searcher_create / _run / _run_host
+* ``autotune_dedisperse``        sp_autotune_dedisperse (kernel shape choice)
+* ``dedisperse_batch``           sp_dedisperse_batch (many beams, one launch)
+* ``Batch``                      sp_batch_* (grouped multi-beam step, graph)
 """
 from __future__ import annotations
 
@@ -64,8 +67,31 @@ SIGNATURES = {
     "sp_searcher_destroy": (ctypes.c_int, [P]),
     "sp_searcher_run": (ctypes.c_int, [P, P, P, I64, P, P]),
     "sp_searcher_run_host": (ctypes.c_int, [P, P, P, I64, P, P]),
+    "sp_dedisp_shape_info": (ctypes.c_int, [I32, P, P, P]),
+    "sp_plan_create_shaped": (ctypes.c_int, [P, I32, F64, P, I32, I32, P]),
+    "sp_plan_shape": (ctypes.c_int, [P, P, P, P]),
+    "sp_autotune_dedisperse": (ctypes.c_int, [P, I32, F64, P, I32, I64, I32, P, P, P]),
+    "sp_dedisperse_batch_workspace_bytes": (I64, [I32]),
+    "sp_dedisperse_batch": (ctypes.c_int, [P, I32, P, I64, P]),
+    "sp_batch_create": (ctypes.c_int, [P, I32, P, P, I32, P, I32, F32, I64, I64, I64, P]),
+    "sp_batch_destroy": (ctypes.c_int, [P]),
+    "sp_batch_info": (ctypes.c_int, [P, P, P]),
+    "sp_batch_input": (ctypes.c_int, [P, I32, P, P]),
+    "sp_batch_run": (ctypes.c_int, [P, I32, P]),
+    "sp_batch_group_ms": (ctypes.c_int, [P, P]),
+    "sp_batch_capture": (ctypes.c_int, [P, I32, P]),
+    "sp_batch_launch": (ctypes.c_int, [P, P]),
+    "sp_batch_results": (ctypes.c_int, [P, I32, P, I64, P, P]),
+    "sp_batch_dmt": (ctypes.c_int, [P, I32, P]),
+    "sp_batch_run_host": (ctypes.c_int, [P, P, P, I64, P, P]),
+    "sp_batch_status": (ctypes.c_int, [P, P, I32]),
     "sp_probe_iadd3_rate": (ctypes.c_int, [ctypes.c_int, P, P]),
 }
+SP_DEDISP_NUM_SHAPES = 3
+SP_SHAPE_AUTO = -1
+SP_AUTOTUNE_SAMPLES = 16384
+SP_AUTOTUNE_REPS = 3
+SP_BATCH_GROUPED, SP_BATCH_PER_BEAM, SP_BATCH_GROUPED_GRID, SP_BATCH_TIMED = 0, 1, 2, 16
 
 
 def _lib():
@@ -113,16 +139,33 @@ def _widths(widths) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
 
 
-class Plan:
-    """Dedispersion plan: delay table of Eq. 1 (rounded half up) and tiling."""
+def shape_info(shape: int):
+    """(DM tile, time tile, channel chunk) of a compiled kernel shape."""
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib().sp_dedisp_shape_info(int(shape), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "sp_dedisp_shape_info")
+    return int(a.value), int(b.value), int(c.value)
 
-    def __init__(self, freqs_mhz, tsamp_s: float, dms):
+
+class Plan:
+    """Dedispersion plan: delay table of Eq. 1 (rounded half up) and tiling.
+    ``shape`` None = sp_plan_create (shape 0); an int = sp_plan_create_shaped
+    (SP_SHAPE_AUTO lets the autotuner choose)."""
+
+    def __init__(self, freqs_mhz, tsamp_s: float, dms, shape: int | None = None):
         f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
         d = np.ascontiguousarray(dms, dtype=np.float64)
         h = ctypes.c_void_p()
-        _check(_lib().sp_plan_create(f.ctypes.data, f.size, float(tsamp_s), d.ctypes.data, d.size,
-                                     ctypes.byref(h)), "sp_plan_create")
+        if shape is None:
+            _check(_lib().sp_plan_create(f.ctypes.data, f.size, float(tsamp_s), d.ctypes.data, d.size,
+                                         ctypes.byref(h)), "sp_plan_create")
+        else:
+            _check(_lib().sp_plan_create_shaped(f.ctypes.data, f.size, float(tsamp_s), d.ctypes.data, d.size,
+                                                int(shape), ctypes.byref(h)), "sp_plan_create_shaped")
         self._h = h
+        sh, nt, sm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib().sp_plan_shape(h, ctypes.byref(sh), ctypes.byref(nt), ctypes.byref(sm)), "sp_plan_shape")
+        self.shape, self.ntiles, self.smem_bytes = int(sh.value), int(nt.value), int(sm.value)
         md, nc, nd = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(_lib().sp_plan_info(h, ctypes.byref(md), ctypes.byref(nc), ctypes.byref(nd)), "sp_plan_info")
         self.max_delay, self.nchan, self.ndm = md.value, nc.value, nd.value
@@ -286,6 +329,160 @@ class Searcher:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib().sp_searcher_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_dedisperse(freqs_mhz, tsamp_s: float, dms, n_out_sample: int = SP_AUTOTUNE_SAMPLES,
+                        reps: int = SP_AUTOTUNE_REPS, stream=None):
+    """Times every kernel shape on this plan; returns (best shape, ms per
+    launch of each shape, +inf where a shape cannot run)."""
+    f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+    d = np.ascontiguousarray(dms, dtype=np.float64)
+    ms = np.empty(SP_DEDISP_NUM_SHAPES, np.float32)
+    best = ctypes.c_int32()
+    _check(_lib().sp_autotune_dedisperse(f.ctypes.data, f.size, float(tsamp_s), d.ctypes.data, d.size,
+                                         int(n_out_sample), int(reps), ms.ctypes.data, ctypes.byref(best),
+                                         _stream(stream)), "sp_autotune_dedisperse")
+    return int(best.value), ms
+
+
+class _CudaArray:
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def _device_view(ptr: int, rows: int, cols: int, typestr: str):
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, (rows, cols), typestr), device="cuda")
+
+
+class _BatchBeam(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("d_staged", ctypes.c_void_p), ("pitch", ctypes.c_int64),
+                ("n_in", ctypes.c_int64), ("d_out", ctypes.c_void_p), ("n_out", ctypes.c_int64)]
+
+
+def dedisperse_batch_workspace_bytes(nbeams: int) -> int:
+    return int(_lib().sp_dedisperse_batch_workspace_bytes(int(nbeams)))
+
+
+def dedisperse_batch(beams, d_work, stream=None):
+    """beams: list of (plan, d_staged, n_in, d_out) with d_staged from
+    staged_buffer(nchan, n_in) (filled by stage_input) and d_out int32
+    [ndm][n_out].  One persistent launch for all of them."""
+    arr = (_BatchBeam * len(beams))()
+    for i, (plan, staged, n_in, out) in enumerate(beams):
+        arr[i] = _BatchBeam(plan.handle.value, _ptr(staged), staged_pitch(int(n_in)), int(n_in), _ptr(out),
+                            int(out.shape[1]))
+    _check(_lib().sp_dedisperse_batch(ctypes.cast(arr, ctypes.c_void_p), len(beams), _ptr(d_work),
+                                      int(d_work.numel()), _stream(stream)), "sp_dedisperse_batch")
+
+
+class Batch:
+    """A fixed set of beams searched as one step (sp_batch_*): grouped
+    persistent dedispersion under a DM-transform memory budget, searches
+    overlapped on a second stream, optional CUDA-graph capture."""
+
+    def __init__(self, plans, beam_plan, beam_n_out, widths, threshold: float, norm_block: int, cand_cap: int,
+                 dmt_budget_bytes: int):
+        self.plans = list(plans)
+        hp = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        bp = np.ascontiguousarray(beam_plan, dtype=np.int32)
+        bn = np.ascontiguousarray(beam_n_out, dtype=np.int64)
+        w = _widths(widths)
+        h = ctypes.c_void_p()
+        _check(_lib().sp_batch_create(ctypes.cast(hp, ctypes.c_void_p), len(self.plans), bp.ctypes.data,
+                                      bn.ctypes.data, bp.size, w.ctypes.data, w.size, float(threshold),
+                                      int(norm_block), int(cand_cap), int(dmt_budget_bytes), ctypes.byref(h)),
+               "sp_batch_create")
+        self._h = h
+        self.nbeams = int(bp.size)
+        self.beam_plan = bp.copy()
+        self.n_out = bn.copy()
+        self.cap = int(cand_cap)
+        ng, nb = ctypes.c_int32(), ctypes.c_int64()
+        _check(_lib().sp_batch_info(h, ctypes.byref(ng), ctypes.byref(nb)), "sp_batch_info")
+        self.ngroups, self.device_bytes = int(ng.value), int(nb.value)
+
+    def input(self, beam: int):
+        """(device address, n_in) of beam's input buffer [n_in][nchan]."""
+        p, n = ctypes.c_void_p(), ctypes.c_int64()
+        _check(_lib().sp_batch_input(self._h, int(beam), ctypes.byref(p), ctypes.byref(n)), "sp_batch_input")
+        return int(p.value), int(n.value)
+
+    def input_tensor(self, beam: int, nchan: int):
+        """torch view (no copy) of beam's input buffer, uint8 [n_in][nchan]."""
+        return _device_view(*self.input(beam), nchan, "|u1")
+
+    def dmt_tensor(self, beam: int, ndm: int):
+        """torch view of beam's DM transform as left by the last run, int32
+        [ndm][n_out] (sp_batch_dmt: only while the arenas still hold it)."""
+        return _device_view(self.dmt_ptr(beam), ndm, int(self.n_out[beam]), "<i4")
+
+    def run(self, mode: int = SP_BATCH_GROUPED, stream=None):
+        _check(_lib().sp_batch_run(self._h, int(mode), _stream(stream)), "sp_batch_run")
+
+    def group_ms(self) -> np.ndarray:
+        """Per-group persistent-launch times (ms) of the last timed run."""
+        out = np.zeros(self.ngroups, np.float32)
+        _check(_lib().sp_batch_group_ms(self._h, out.ctypes.data), "sp_batch_group_ms")
+        return out
+
+    def capture(self, mode: int = SP_BATCH_GROUPED, stream=None):
+        _check(_lib().sp_batch_capture(self._h, int(mode), _stream(stream)), "sp_batch_capture")
+
+    def launch(self, stream=None):
+        _check(_lib().sp_batch_launch(self._h, _stream(stream)), "sp_batch_launch")
+
+    def results(self, beam: int, stream=None) -> np.ndarray:
+        """Candidates of one beam (structured array sorted by (dm_idx, t))."""
+        buf = np.zeros((max(self.cap, 1), 4), np.int32)
+        cnt = ctypes.c_int64()
+        rc = _lib().sp_batch_results(self._h, int(beam), buf.ctypes.data, self.cap, ctypes.byref(cnt),
+                                     _stream(stream))
+        if rc not in (SP_OK, SP_EOVERFLOW):
+            _check(rc, "sp_batch_results")
+        return cands_to_numpy(buf, int(cnt.value))
+
+    def count(self, beam: int, stream=None) -> int:
+        cnt = ctypes.c_int64()
+        rc = _lib().sp_batch_results(self._h, int(beam), None, 0, ctypes.byref(cnt), _stream(stream))
+        if rc not in (SP_OK, SP_EOVERFLOW):
+            _check(rc, "sp_batch_results")
+        return int(cnt.value)
+
+    def dmt_ptr(self, beam: int) -> int:
+        p = ctypes.c_void_p()
+        _check(_lib().sp_batch_dmt(self._h, int(beam), ctypes.byref(p)), "sp_batch_dmt")
+        return int(p.value)
+
+    def run_host(self, h_inputs, h_cands: np.ndarray, stream=None) -> np.ndarray:
+        """h_inputs: per beam a host uint8 [n_in][nchan] array or pinned CPU
+        tensor; h_cands: int32 [nbeams * cap_per_beam][4].  Returns the
+        per-beam counts."""
+        arr = (ctypes.c_void_p * self.nbeams)(*[_ptr(x) for x in h_inputs])
+        counts = np.zeros(self.nbeams, np.int64)
+        cap_pb = h_cands.shape[0] // self.nbeams
+        rc = _lib().sp_batch_run_host(self._h, ctypes.cast(arr, ctypes.c_void_p), h_cands.ctypes.data, cap_pb,
+                                      counts.ctypes.data, _stream(stream))
+        if rc not in (SP_OK, SP_EOVERFLOW):
+            _check(rc, "sp_batch_run_host")
+        return counts
+
+    def status(self, clear: bool = False) -> int:
+        v = ctypes.c_int32()
+        _check(_lib().sp_batch_status(self._h, ctypes.byref(v), int(clear)), "sp_batch_status")
+        return int(v.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().sp_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -8,7 +8,7 @@
 
 using namespace sp;
 
-namespace {
+namespace sp {
 
 bool on_plan_device(const sp_plan *p) {
     int dev = -1;
@@ -29,6 +29,10 @@ int check_widths(const int32_t *w, int32_t nw) {
     }
     return SP_OK;
 }
+
+}  // namespace sp
+
+namespace {
 
 int sps_common(const int32_t *d_dmt, int32_t ndm, int64_t n_out, const int32_t *h_widths, int32_t nw,
                int64_t norm_block, void *d_work, int64_t work_bytes, SpsArgs &a) {
@@ -81,8 +85,7 @@ extern "C" int64_t sp_dedisperse_workspace_bytes(const sp_plan *p, int64_t n_in)
 static int check_dedisp_shape(const sp_plan *p, int64_t n_in, int64_t n_out) {
     if (!on_plan_device(p)) return SP_EINVAL;
     if (n_out != n_in - p->max_delay) return SP_ESHAPE;
-    if (n_in > (int64_t)INT32_MAX - 4096 || (n_out + kDedispTimeTile - 1) / kDedispTimeTile > 65535)
-        return SP_ELIMIT;
+    if (n_in > (int64_t)INT32_MAX - 4096 || dedisp_time_tiles(p, n_out) > 65535) return SP_ELIMIT;
     return SP_OK;
 }
 

@@ -4,23 +4,27 @@
 //
 //   out[d][t] = sum_c in[t + delay[d][c]][c]
 //
-// Two kernels:
+// Kernels:
 //   stage_input_kernel  time-major [n_in][nchan] -> channel-major
 //                       [nchan][pitch] (zero padded), so that one channel's
 //                       time series is contiguous.
-//   dedisperse_kernel   one CTA = up to 32 consecutive trial DMs (a "DM tile"
-//                       from the plan) x 512 output samples.  Channels go in
-//                       chunks of 8: per channel the CTA stages the window of
-//                       input samples the tile's delays reach (512 + delay
-//                       spread + alignment slack).  Warp 0 fetches chunk k+2
-//                       with bulk asynchronous copies (TMA) into a ring of
-//                       three raw slots while the CTA sums chunk k, so every
-//                       fetch has two chunks of work to land in; each warp
-//                       expands one channel of chunk k+1 into four copies
-//                       shifted by 0..3 bytes (double-buffered), so that any
-//                       4 consecutive samples are one aligned 32-bit load.
-//                       One barrier per chunk.  One staged byte serves up to
-//                       32 DMs.
+//   dedisperse_kernel   one CTA = up to DT = 4*CH consecutive trial DMs (a "DM
+//                       tile" from the plan) x T = 32*SPT output samples, for
+//                       a compiled shape (CH, SPT).  Channels go in chunks of
+//                       CH: per channel the CTA stages the window of input
+//                       samples the tile's delays reach (T + delay spread +
+//                       alignment slack).  Warp 0 fetches chunk k+2 with bulk
+//                       asynchronous copies (TMA) into a ring of three raw
+//                       slots while the CTA sums chunk k, so every fetch has
+//                       two chunks of work to land in; each warp expands one
+//                       channel of chunk k+1 into four copies shifted by 0..3
+//                       bytes (double-buffered), so that any 4 consecutive
+//                       samples are one aligned 32-bit load.  One barrier per
+//                       chunk.  One staged byte serves up to DT DMs.
+//   dedisperse_batch_kernel  the same tile body in a persistent grid that
+//                       takes (beam, DM tile, time tile) items from a work
+//                       queue: many beams of uneven length and DM range in
+//                       one launch.
 //
 // Arithmetic: the sum is a pure integer add of bytes (no tensor-core
 // contraction exists here).  Each thread owns 4 DMs x 16 samples.  For every
@@ -28,6 +32,9 @@
 // channel, transposes the 4x4 bytes with byte permutes, and adds each
 // 4-channel word into an int32 accumulator with one 4-way byte dot product:
 // four channel adds per instruction, exact (every sum is at most 255*nchan).
+#include <algorithm>
+#include <mutex>
+
 #include "sp_internal.h"
 
 namespace sp {
@@ -138,72 +145,82 @@ __device__ __forceinline__ void add_quad(uint32_t wa, uint32_t wb, uint32_t wc, 
     acc[3] = (int32_t)__dp4a(__byte_perm(t1, t3, 0x7632), 0x01010101u, (uint32_t)acc[3]);
 }
 
-// Shared-memory layout (bytes):
+// Shared-memory layout (bytes), for a shape with CH channels per chunk and
+// DT = 4*CH trial DMs per tile:
 //   [0, 8*NS)                 one mbarrier per raw slot
+//   [32, 40)                  work item of a persistent CTA
 //   [64, 64 + NS*CH*16)       geometry of the chunk in each raw slot
 //   [512, 512 + NS*CH*DT*4)   offset table of the chunk in each raw slot
 //   then raw[NS][raw_max]     raw channel rows as copied from global memory
 //   then copies[2][copies_max] per channel four copies of stride R:
 //                             copy r, word j = staged bytes [4j + r, 4j + r + 4)
 //
-// Iteration k: warp 0 issues chunk k+2 into raw slot (k+2) % NS; every warp
-// sums chunk k from copies buffer k & 1, then waits for chunk k+1's bytes and
-// expands its channel of it into copies buffer (k+1) & 1; barrier.  A raw
-// slot is refilled two barriers after its chunk was expanded; a copies
-// buffer one barrier after its chunk was summed.
-template <int NDT, int NWARP, int CH>
-__global__ void __launch_bounds__(NWARP * 32, 2)
-dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, int32_t nchunks,
-                  const int32_t *__restrict__ tile_first, const int32_t *__restrict__ tile_count,
-                  const int4 *__restrict__ chunk_geo, const int32_t *__restrict__ chunk_off, int32_t copies_max,
-                  int32_t raw_max, int64_t n_out, int32_t *__restrict__ out, int32_t *__restrict__ status) {
+// Chunks are numbered across all tiles a CTA processes (seq0 + k), so that
+// a persistent CTA keeps using its mbarriers: chunk g lives in raw slot
+// g % NS and completes phase (g / NS) & 1 of that slot's barrier.
+//
+// Iteration k: warp 0 issues chunk k+2; every warp sums chunk k from copies
+// buffer k & 1, then waits for chunk k+1's bytes and expands its channel of
+// it into copies buffer (k+1) & 1; barrier.  A raw slot is refilled two
+// barriers after its chunk was expanded; a copies buffer one barrier after
+// its chunk was summed.
+template <int CH, int SPT>
+struct Shape {
+    static constexpr int NDT = kDedispDmPerThread;
+    static constexpr int DT = NDT * CH;
+    static constexpr int T = 32 * SPT;
+    static constexpr int NQ = SPT / 4;  // 4-sample words per thread per row
+    static constexpr int NS = kDedispRawSlots;
+    static constexpr int HDR = dedisp_header_bytes(CH, DT);
+    static constexpr int GROUP = kDedispTileGroupDms / DT;  // DM tiles per raster group
     static_assert(NDT == 4, "offset table is read as int4 per thread");
-    constexpr int DT = NDT * NWARP;
-    constexpr int T = kDedispTimeTile;
-    constexpr int NS = kDedispRawSlots;
-    static_assert(T == 32 * 16, "a warp spans the time tile: 32 lanes x 16 samples");
-    static_assert(CH <= 31 && NWARP == CH && CH % 4 == 0, "warp 0 lanes issue one channel each; one warp per channel");
-    static_assert(DT == kDedispDmTile && CH == kDedispChanChunk, "layout shared with the plan");
-    static_assert(8 * NS <= kDedispGeoOffset, "mbarriers overlap the geometry ring");
+    static_assert(SPT % 4 == 0 && T <= kDedispMaxTimeTile, "time tile");
+    static_assert(CH <= kDedispMaxChanChunk && CH % 4 == 0, "warp 0 lanes issue one channel each; quads");
+    static_assert(8 * NS <= kDedispItemOffset && kDedispItemOffset + 8 <= kDedispGeoOffset,
+                  "mbarriers, work item and geometry ring overlap");
     static_assert(kDedispGeoOffset + NS * CH * 16 <= kDedispOffTabOffset, "geometry ring overlaps the offsets");
+    static_assert(HDR % 128 == 0, "raw slots start 128-byte aligned");
+};
 
-    extern __shared__ __align__(128) uint8_t smem[];
+// Maps the id of a (DM tile, time tile) pair of one beam to the pair.
+// Groups of G DM tiles sweep all time tiles, so the CTAs resident at one
+// time share an input window that fits in L2 (DM-tile-fastest order would
+// make them span the whole dispersion sweep).
+__device__ __forceinline__ void raster(int64_t id, int ntiles, int64_t ntime, int G, int &tile, int64_t &tq) {
+    const int64_t per_group = (int64_t)G * ntime;
+    const int group = (int)(id / per_group);
+    const int64_t r = id - group * per_group;
+    const int width = min(G, ntiles - group * G);
+    tile = group * G + (int)(r % width);
+    tq = r / width;
+}
+
+// One (DM tile, time tile) of one beam.  Returns false (uniformly across the
+// CTA) if a staging wait ran out; copies still in flight are waited for
+// (with the same bound) before it returns.
+template <int CH, int SPT>
+__device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const uint8_t *__restrict__ xt,
+                                            int64_t pitch, int32_t nchan, int32_t nchunks, int d_first, int d_cnt,
+                                            int64_t t0, const int4 *__restrict__ geo_g,
+                                            const int32_t *__restrict__ off_g, int32_t copies_max,
+                                            int32_t raw_max, int64_t n_out, int32_t *__restrict__ out) {
+    using S = Shape<CH, SPT>;
+    constexpr int NDT = S::NDT, DT = S::DT, NS = S::NS, NQ = S::NQ;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);                       // [NS]
     int4 *geo_s = reinterpret_cast<int4 *>(smem + kDedispGeoOffset);           // [NS][CH]
     int32_t *offt_s = reinterpret_cast<int32_t *>(smem + kDedispOffTabOffset);  // [NS][CH*DT]
-    uint8_t *raw_s = smem + kDedispHeaderBytes;                                 // [NS][raw_max]
+    uint8_t *raw_s = smem + S::HDR;                                             // [NS][raw_max]
     uint8_t *cop_s = raw_s + NS * raw_max;                                      // [2][copies_max]
 
-    // Raster: groups of kDedispTileGroup DM tiles sweep all time tiles, so
-    // the CTAs resident at one time share an input window that fits in L2
-    // (DM-tile-fastest order would make them span the whole sweep).
-    int tile;
-    int64_t t0;
-    {
-        const int ntiles = gridDim.x, ntime = gridDim.y;
-        const int64_t id = (int64_t)blockIdx.y * ntiles + blockIdx.x;
-        const int64_t per_group = (int64_t)kDedispTileGroup * ntime;
-        const int group = (int)(id / per_group);
-        const int64_t r = id - group * per_group;
-        const int width = min(kDedispTileGroup, ntiles - group * kDedispTileGroup);
-        tile = group * kDedispTileGroup + (int)(r % width);
-        t0 = (r / width) * T;
-    }
-    const int d_first = tile_first[tile];
-    const int d_cnt = tile_count[tile];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const bool warp_active = warp * NDT < d_cnt;
-    const int4 *geo_g = chunk_geo + (int64_t)tile * nchunks * CH;
-    const int32_t *off_g = chunk_off + (int64_t)tile * nchunks * CH * DT;
     const int4 zero4 = make_int4(0, 0, 0, 0);
 
-    if (threadIdx.x < NS) mbar_init(&mbar[threadIdx.x], 1);
-    if (threadIdx.x == 0) fence_mbar_init();
-    __syncthreads();
-
-    auto issue = [&](int kk, int4 g) {  // warp 0; chunk kk into raw slot kk % NS
-        const int sl = kk % NS;
+    auto slot_of = [&](int kk) { return (int)((seq0 + (uint32_t)kk) % NS); };
+    auto parity_of = [&](int kk) { return ((seq0 + (uint32_t)kk) / NS) & 1u; };
+    auto issue = [&](int kk, int4 g) {  // warp 0; chunk kk into its raw slot
+        const int sl = slot_of(kk);
         const int nc = min(CH, nchan - kk * CH);
         uint32_t bytes = (lane < nc) ? (uint32_t)g.y + 16u : 0u;
 #pragma unroll
@@ -221,13 +238,13 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
         return (kk < nchunks && lane < CH && kk * CH + lane < nchan) ? __ldg(geo_g + (int64_t)kk * CH + lane)
                                                                       : zero4;
     };
-    // Four shifted copies of this warp's channel of chunk kk, from raw slot
-    // kk % NS into copies buffer kk & 1.
+    // Four shifted copies of this warp's channel of chunk kk, from its raw
+    // slot into copies buffer kk & 1.
     auto build = [&](int kk) {
-        const int sl = kk % NS;
+        const int sl = slot_of(kk);
         if (kk * CH + warp >= nchan) return;
         const int4 g = geo_s[sl * CH + warp];
-        const int32_t R = g.y, S = g.y;
+        const int32_t R = g.y, Sd = g.y;
         const uint8_t *src = raw_s + sl * raw_max + g.w;
         uint8_t *row = cop_s + (kk & 1) * copies_max + g.z;
         const int nseg = R / 16;
@@ -240,19 +257,18 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
             if (act && (lane == 31 || q + 1 >= nseg)) e = *reinterpret_cast<const uint32_t *>(src + 16 * q + 16);
             if (act) {
                 *reinterpret_cast<uint4 *>(row + 16 * q) = a;
-                *reinterpret_cast<uint4 *>(row + S + 16 * q) =
+                *reinterpret_cast<uint4 *>(row + Sd + 16 * q) =
                     make_uint4(__byte_perm(a.x, a.y, 0x4321), __byte_perm(a.y, a.z, 0x4321),
                                __byte_perm(a.z, a.w, 0x4321), __byte_perm(a.w, e, 0x4321));
-                *reinterpret_cast<uint4 *>(row + 2 * S + 16 * q) =
+                *reinterpret_cast<uint4 *>(row + 2 * Sd + 16 * q) =
                     make_uint4(__byte_perm(a.x, a.y, 0x5432), __byte_perm(a.y, a.z, 0x5432),
                                __byte_perm(a.z, a.w, 0x5432), __byte_perm(a.w, e, 0x5432));
-                *reinterpret_cast<uint4 *>(row + 3 * S + 16 * q) =
+                *reinterpret_cast<uint4 *>(row + 3 * Sd + 16 * q) =
                     make_uint4(__byte_perm(a.x, a.y, 0x6543), __byte_perm(a.y, a.z, 0x6543),
                                __byte_perm(a.z, a.w, 0x6543), __byte_perm(a.w, e, 0x6543));
             }
         }
     };
-
     int4 g_next = zero4;  // warp 0: geometry of the next chunk to issue
     if (warp == 0) {
         const int4 g0 = load_geo(0), g1 = load_geo(1);
@@ -261,31 +277,41 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
         if (nchunks > 1) issue(1, g1);
     }
     __syncthreads();
+    // A wait that runs out sets `failed`.  Later iterations then issue and
+    // sum nothing; they wait again (bounded) for the chunk that timed out and
+    // then for every chunk already issued, so that no copy lands in shared
+    // memory after the CTA has left.  A second timeout gives up waiting.
+    int last_issued = min(nchunks, 2) - 1;
+    int pending = 0;  // next chunk to wait for
+    bool failed = false;
     {
-        const bool ok = mbar_wait_bounded(&mbar[0], 0u);
-        if (ok) build(0);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) atomicOr(status, SP_STATUS_STAGING_TIMEOUT);
-            return;
+        const bool ok = mbar_wait_bounded(&mbar[slot_of(0)], parity_of(0));
+        if (ok) {
+            build(0);
+            pending = 1;
         }
+        failed = __syncthreads_or(!ok);
     }
 
-    int32_t acc[NDT][16];
+    int32_t acc[NDT][SPT];
 #pragma unroll
     for (int i = 0; i < NDT; ++i)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[i][j] = 0;
+        for (int j = 0; j < SPT; ++j) acc[i][j] = 0;
 
     for (int k = 0; k < nchunks; ++k) {
         const int b = k & 1;
         const int nc = min(CH, nchan - k * CH);
-        if (warp == 0 && k + 2 < nchunks) {
-            issue(k + 2, g_next);
-            g_next = load_geo(k + 3);
+        if (!failed && k + 2 < nchunks) {
+            last_issued = k + 2;
+            if (warp == 0) {
+                issue(k + 2, g_next);
+                g_next = load_geo(k + 3);
+            }
         }
-        if (warp_active) {
+        if (warp_active && !failed) {
             const uint8_t *sb = cop_s + b * copies_max + lane * 4;
-            const int32_t *ot = offt_s + (k % NS) * CH * DT + warp * NDT;
+            const int32_t *ot = offt_s + slot_of(k) * CH * DT + warp * NDT;
             if (nc == CH) {
 #pragma unroll
                 for (int qd = 0; qd < CH / 4; ++qd) {
@@ -298,7 +324,7 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
 #pragma unroll
                     for (int i = 0; i < NDT; ++i) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q < NQ; ++q) {
                             const uint32_t wa = *reinterpret_cast<const uint32_t *>(sb + a0[i] + 128 * q);
                             const uint32_t wb = *reinterpret_cast<const uint32_t *>(sb + a1[i] + 128 * q);
                             const uint32_t wc = *reinterpret_cast<const uint32_t *>(sb + a2[i] + 128 * q);
@@ -314,7 +340,7 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
 #pragma unroll
                     for (int i = 0; i < NDT; ++i) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q < NQ; ++q) {
                             const uint32_t w = *reinterpret_cast<const uint32_t *>(sb + ac[i] + 128 * q);
                             add_quad(w, 0u, 0u, 0u, &acc[i][4 * q]);
                         }
@@ -323,15 +349,18 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
             }
         }
         bool ok = true;
-        if (k + 1 < nchunks) {
-            ok = mbar_wait_bounded(&mbar[(k + 1) % NS], (uint32_t)((k + 1) / NS) & 1u);
-            if (ok) build(k + 1);
+        if (pending <= last_issued) {
+            ok = mbar_wait_bounded(&mbar[slot_of(pending)], parity_of(pending));
+            if (ok) {
+                if (!failed) build(pending);
+                ++pending;
+            } else if (failed) {
+                pending = last_issued + 1;
+            }
         }
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) atomicOr(status, SP_STATUS_STAGING_TIMEOUT);
-            return;
-        }
+        failed = __syncthreads_or(failed || !ok);
     }
+    if (failed) return false;
 
     const bool vec = (n_out & 3) == 0;
 #pragma unroll
@@ -340,7 +369,7 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
         if (dl >= d_cnt) continue;
         int32_t *orow = out + (int64_t)(d_first + dl) * n_out;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int64_t t = t0 + 128 * q + 4 * lane;
             if (vec && t + 3 < n_out) {
                 *reinterpret_cast<int4 *>(orow + t) =
@@ -352,13 +381,129 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
             }
         }
     }
+    return true;
 }
 
-using DedispKernel = void (*)(const uint8_t *, int64_t, int32_t, int32_t, const int32_t *, const int32_t *,
-                              const int4 *, const int32_t *, int32_t, int32_t, int64_t, int32_t *, int32_t *);
-constexpr DedispKernel kDedisp = dedisperse_kernel<kDedispDmPerThread, kDedispWarps, kDedispChanChunk>;
+template <int CH, int SPT>
+__device__ __forceinline__ void init_barriers(uint8_t *smem) {
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    if (threadIdx.x < kDedispRawSlots) mbar_init(&mbar[threadIdx.x], 1);
+    if (threadIdx.x == 0) fence_mbar_init();
+    __syncthreads();
+}
 
+// One beam: grid = (DM tiles, time tiles), one (DM tile, time tile) per CTA
+// in raster order.
+template <int CH, int SPT>
+__global__ void __launch_bounds__(CH * 32, (CH == 8 ? 2 : 3))
+dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, int32_t nchunks,
+                  const int32_t *__restrict__ tile_first, const int32_t *__restrict__ tile_count,
+                  const int4 *__restrict__ chunk_geo, const int32_t *__restrict__ chunk_off, int32_t copies_max,
+                  int32_t raw_max, int64_t n_out, int32_t *__restrict__ out, int32_t *__restrict__ status) {
+    using S = Shape<CH, SPT>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    int tile;
+    int64_t tq;
+    raster((int64_t)blockIdx.y * gridDim.x + blockIdx.x, (int)gridDim.x, (int64_t)gridDim.y, S::GROUP, tile, tq);
+    init_barriers<CH, SPT>(smem);
+    const bool ok = dedisp_tile<CH, SPT>(smem, 0u, xt, pitch, nchan, nchunks, tile_first[tile], tile_count[tile],
+                                         tq * S::T, chunk_geo + (int64_t)tile * nchunks * CH,
+                                         chunk_off + (int64_t)tile * nchunks * CH * S::DT, copies_max, raw_max,
+                                         n_out, out);
+    if (!ok && threadIdx.x == 0) atomicOr(status, SP_STATUS_STAGING_TIMEOUT);
+}
 
+// Many beams in one launch.  Items are (beam, DM tile, time tile), numbered
+// beam by beam and, within a beam, in the raster order of the grid kernel;
+// beams may differ in length, DM list and channel count but share the kernel
+// shape.  Persistent (counter != nullptr): each CTA takes items from a work
+// queue (one atomic per item) until it is empty.  Otherwise one item per
+// CTA (item = blockIdx.x), so that CTAs retire and the block scheduler can
+// interleave other kernels' CTAs between them.
+template <int CH, int SPT>
+__global__ void __launch_bounds__(CH * 32, (CH == 8 ? 2 : 3))
+dedisperse_batch_kernel(const BatchBeamDev *__restrict__ beams, const int64_t *__restrict__ item_begin,
+                        int32_t nbeams, int64_t nitems, unsigned long long *__restrict__ counter,
+                        int32_t copies_max, int32_t raw_max, int32_t *__restrict__ status) {
+    using S = Shape<CH, SPT>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    long long *s_item = reinterpret_cast<long long *>(smem + kDedispItemOffset);
+    init_barriers<CH, SPT>(smem);
+    uint32_t seq = 0;
+    for (int pass = 0;; ++pass) {
+        if (counter) {
+            if (threadIdx.x == 0) *s_item = (long long)atomicAdd(counter, 1ull);
+        } else if (threadIdx.x == 0) {
+            *s_item = pass == 0 ? (long long)blockIdx.x : (long long)nitems;
+        }
+        __syncthreads();
+        const int64_t item = *s_item;  // thread 0 rewrites it only after the tile's barriers
+        if (item >= nitems) break;
+        int lo = 0, hi = nbeams - 1;  // last beam whose first item is <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(item_begin + mid) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchBeamDev &bm = beams[lo];
+        const int32_t nchunks = bm.nchunks;
+        int tile;
+        int64_t tq;
+        raster(item - __ldg(item_begin + lo), bm.ntiles, (int64_t)bm.ntime, S::GROUP, tile, tq);
+        const bool ok = dedisp_tile<CH, SPT>(smem, seq, bm.xt, bm.pitch, bm.nchan, nchunks, __ldg(bm.tile_first + tile),
+                                             __ldg(bm.tile_count + tile), tq * S::T,
+                                             bm.geo + (int64_t)tile * nchunks * CH,
+                                             bm.off + (int64_t)tile * nchunks * CH * S::DT, copies_max, raw_max,
+                                             bm.n_out, bm.out);
+        if (!ok) {
+            if (threadIdx.x == 0) atomicOr(status, SP_STATUS_STAGING_TIMEOUT);
+            return;
+        }
+        seq += (uint32_t)nchunks;
+    }
+}
+
+using GridKernel = void (*)(const uint8_t *, int64_t, int32_t, int32_t, const int32_t *, const int32_t *,
+                            const int4 *, const int32_t *, int32_t, int32_t, int64_t, int32_t *, int32_t *);
+using BatchKernel = void (*)(const BatchBeamDev *, const int64_t *, int32_t, int64_t, unsigned long long *, int32_t,
+                             int32_t, int32_t *);
+struct ShapeKernels {
+    GridKernel grid;
+    BatchKernel batch;
+    int threads;
+    int time_tile;
+};
+template <int CH, int SPT>
+constexpr ShapeKernels shape_kernels() {
+    return {dedisperse_kernel<CH, SPT>, dedisperse_batch_kernel<CH, SPT>, CH * 32, Shape<CH, SPT>::T};
+}
+static_assert(kDedispNumShapes == 3 && kDedispShapeCh[0] == 8 && kDedispShapeSpt[0] == 16 &&
+                  kDedispShapeCh[1] == 8 && kDedispShapeSpt[1] == 8 && kDedispShapeCh[2] == 4 &&
+                  kDedispShapeSpt[2] == 16,
+              "compiled shapes match the shape table");
+const ShapeKernels kShapes[kDedispNumShapes] = {shape_kernels<8, 16>(), shape_kernels<8, 8>(),
+                                                shape_kernels<4, 16>()};
+
+constexpr int kMaxDev = 64;
+std::mutex g_cfg_lock;
+int g_cfg_smem[kMaxDev][kDedispNumShapes] = {};  // configured dynamic smem per (device, shape)
+
+int configure_shape(int shape, int smem_bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SP_ECUDA;
+    if (dev < 0 || dev >= kMaxDev || shape < 0 || shape >= kDedispNumShapes) return SP_ELIMIT;
+    std::lock_guard<std::mutex> guard(g_cfg_lock);
+    if (g_cfg_smem[dev][shape] >= smem_bytes) return SP_OK;
+    if (cudaFuncSetAttribute(kShapes[shape].grid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(kShapes[shape].batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return SP_ECUDA;
+    }
+    g_cfg_smem[dev][shape] = smem_bytes;
+    return SP_OK;
+}
 
 }  // namespace
 
@@ -369,21 +514,56 @@ int launch_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
+int64_t dedisp_time_tiles(const sp_plan *plan, int64_t n_out) {
+    return (n_out + plan->time_tile - 1) / plan->time_tile;
+}
+
+int dedisp_configure(const sp_plan *plan) { return configure_shape(plan->shape, plan->smem_bytes); }
+
 int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, int64_t n_out, int32_t *d_out,
                       cudaStream_t stream) {
-    static int configured_smem[64] = {0};
-    const int dev = plan->device < 64 ? plan->device : 63;
-    if (configured_smem[dev] < plan->smem_bytes) {
-        if (cudaFuncSetAttribute(kDedisp, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem_bytes) !=
-            cudaSuccess)
-            return SP_ECUDA;
-        configured_smem[dev] = plan->smem_bytes;
+    int rc = dedisp_configure(plan);
+    if (rc) return rc;
+    const ShapeKernels &k = kShapes[plan->shape];
+    const dim3 grid((unsigned)plan->ntiles, (unsigned)dedisp_time_tiles(plan, n_out));
+    k.grid<<<grid, k.threads, plan->smem_bytes, stream>>>(d_xt, pitch, plan->nchan, plan->nchunks,
+                                                          plan->d_tile_first, plan->d_tile_count,
+                                                          plan->d_chunk_geo, plan->d_chunk_off, plan->copies_max,
+                                                          plan->raw_max, n_out, d_out, plan->d_status);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+// Persistent grid: as many CTAs as fit on the device at once.
+int batch_grid(BatchLaunch &b) {
+    if (b.shape < 0 || b.shape >= kDedispNumShapes) return SP_EINVAL;
+    int rc = configure_shape(b.shape, b.smem_bytes);
+    if (rc) return rc;
+    const ShapeKernels &k = kShapes[b.shape];
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.batch, k.threads, b.smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SP_ECUDA;
     }
-    const int64_t ntime = (n_out + kDedispTimeTile - 1) / kDedispTimeTile;
-    const dim3 grid((unsigned)plan->ntiles, (unsigned)ntime);
-    kDedisp<<<grid, kDedispWarps * 32, plan->smem_bytes, stream>>>(
-        d_xt, pitch, plan->nchan, plan->nchunks, plan->d_tile_first, plan->d_tile_count, plan->d_chunk_geo,
-        plan->d_chunk_off, plan->copies_max, plan->raw_max, n_out, d_out, plan->d_status);
+    if (per_sm < 1) return SP_ELIMIT;
+    b.grid = nsm * per_sm;
+    return SP_OK;
+}
+
+int launch_dedisperse_batch(const BatchLaunch &b, cudaStream_t stream, bool persistent) {
+    if (b.shape < 0 || b.shape >= kDedispNumShapes || b.grid < 1) return SP_EINVAL;
+    const ShapeKernels &k = kShapes[b.shape];
+    int64_t grid = std::max<int64_t>(b.nitems, 1);
+    if (persistent) {
+        if (cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess) return SP_ECUDA;
+        grid = std::min<int64_t>(b.grid, grid);
+    } else if (grid > INT32_MAX) {
+        return SP_ELIMIT;
+    }
+    k.batch<<<(unsigned)grid, k.threads, b.smem_bytes, stream>>>(b.d_beams, b.d_item_begin, b.nbeams, b.nitems,
+                                                                 persistent ? b.d_counter : nullptr, b.copies_max,
+                                                                 b.raw_max, b.d_status);
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

@@ -48,7 +48,7 @@ int compute_delays(const double *freqs, int32_t nchan, double tsamp, const doubl
 }
 
 // Staging tables of the dedispersion kernel, per (DM tile, channel chunk).
-// Time tiles start at multiples of kDedispTimeTile (a multiple of 16), so the
+// Time tiles start at multiples of the time tile (a multiple of 16), so the
 // 16-byte-aligned window start of a channel relative to the time tile is
 // (min delay over the tile) rounded down to 16 and does not depend on the
 // time tile; neither do the offsets derived from it.  A channel occupies
@@ -57,7 +57,7 @@ int compute_delays(const double *freqs, int32_t nchan, double tsamp, const doubl
 // byte-shifted copies, stride R).
 void build_chunk_tables(const sp_plan &p, std::vector<int32_t> &geo, std::vector<int32_t> &off,
                         int32_t *copies_max, int32_t *raw_max) {
-    const int32_t CH = kDedispChanChunk, DT = kDedispDmTile;
+    const int32_t CH = p.chan_chunk, DT = p.dm_tile;
     geo.assign((size_t)p.ntiles * p.nchunks * CH * 4, 0);
     off.assign((size_t)p.ntiles * p.nchunks * CH * DT, 0);
     int32_t cmax = 0, rmax = 0;
@@ -76,7 +76,7 @@ void build_chunk_tables(const sp_plan &p, std::vector<int32_t> &geo, std::vector
                     hi = std::max(hi, v);
                 }
                 const int32_t rel_base = lo & ~15;
-                const int32_t R = dedisp_row_bytes(hi - lo);
+                const int32_t R = dedisp_row_bytes(hi - lo, p.time_tile);
                 const int32_t stride = R;  // copies are derived from the raw slot: no tail needed
                 int32_t *g = &geo[(((size_t)j * p.nchunks + k) * CH + i) * 4];
                 g[0] = rel_base;
@@ -125,10 +125,11 @@ static int upload(T **dst, const T *src, size_t n) {
     return SP_OK;
 }
 
-extern "C" int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsamp_s,
-                              const double *dms, int32_t ndm, sp_plan **out) {
+static int create_plan(const double *freqs_mhz, int32_t nchan, double tsamp_s, const double *dms, int32_t ndm,
+                       int32_t shape, sp_plan **out) {
     if (!out) return SP_EINVAL;
     *out = nullptr;
+    if (shape < 0 || shape >= kDedispNumShapes) return SP_EINVAL;
     sp_plan *p = new (std::nothrow) sp_plan();
     if (!p) return SP_ENOMEM;
     int rc = compute_delays(freqs_mhz, nchan, tsamp_s, dms, ndm, p->delays, &p->max_delay);
@@ -139,11 +140,15 @@ extern "C" int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsa
     p->nchan = nchan;
     p->ndm = ndm;
     p->tsamp = tsamp_s;
+    p->shape = shape;
+    p->chan_chunk = kDedispShapeCh[shape];
+    p->dm_tile = kDedispDmPerThread * p->chan_chunk;
+    p->time_tile = 32 * kDedispShapeSpt[shape];
 
     // DM tiles: greedy runs of consecutive trial DMs (list order) with at
-    // most kDedispDmTile members and a per-channel delay spread (max - min
-    // over the run) of at most kDedispMaxSpan samples.  A single DM has
-    // spread 0, so every plan tiles.
+    // most dm_tile members and a per-channel delay spread (max - min over
+    // the run) of at most kDedispMaxSpan samples.  A single DM has spread 0,
+    // so every plan tiles.
     std::vector<int32_t> lo(nchan), hi(nchan);
     int32_t d = 0;
     while (d < ndm) {
@@ -151,7 +156,7 @@ extern "C" int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsa
         std::copy(row, row + nchan, lo.begin());
         std::copy(row, row + nchan, hi.begin());
         int32_t cnt = 1;
-        while (cnt < kDedispDmTile && d + cnt < ndm) {
+        while (cnt < p->dm_tile && d + cnt < ndm) {
             const int32_t *r2 = &p->delays[(size_t)(d + cnt) * nchan];
             bool ok = true;
             for (int32_t c = 0; c < nchan && ok; ++c) {
@@ -170,15 +175,21 @@ extern "C" int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsa
         d += cnt;
     }
     p->ntiles = (int32_t)p->tile_first.size();
-    p->nchunks = (nchan + kDedispChanChunk - 1) / kDedispChanChunk;
+    p->nchunks = (nchan + p->chan_chunk - 1) / p->chan_chunk;
     std::vector<int32_t> geo, off;
     build_chunk_tables(*p, geo, off, &p->copies_max, &p->raw_max);
-    p->smem_bytes = kDedispHeaderBytes + kDedispRawSlots * p->raw_max + 2 * p->copies_max;
+    p->smem_bytes = dedisp_header_bytes(p->chan_chunk, p->dm_tile) + kDedispRawSlots * p->raw_max + 2 * p->copies_max;
 
-    if (cudaGetDevice(&p->device) != cudaSuccess) {
+    int smem_optin = 0;
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess) {
         cudaGetLastError();
         delete p;
         return SP_ECUDA;
+    }
+    if (p->smem_bytes > smem_optin) {  // cannot happen with the compiled shapes and kDedispMaxSpan
+        delete p;
+        return SP_ELIMIT;
     }
     rc = upload(&p->d_delays, p->delays.data(), p->delays.size());
     if (!rc) rc = upload(&p->d_tile_first, p->tile_first.data(), p->tile_first.size());
@@ -187,12 +198,45 @@ extern "C" int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsa
     if (!rc) rc = upload(&p->d_chunk_off, off.data(), off.size());
     const int32_t zero = 0;
     if (!rc) rc = upload(&p->d_status, &zero, 1);
+    if (!rc) rc = dedisp_configure(p);
     if (rc) {
         free_plan_device(p);
         delete p;
         return rc;
     }
     *out = p;
+    return SP_OK;
+}
+
+extern "C" int sp_plan_create(const double *freqs_mhz, int32_t nchan, double tsamp_s, const double *dms,
+                              int32_t ndm, sp_plan **out) {
+    return create_plan(freqs_mhz, nchan, tsamp_s, dms, ndm, 0, out);
+}
+
+extern "C" int sp_plan_create_shaped(const double *freqs_mhz, int32_t nchan, double tsamp_s, const double *dms,
+                                     int32_t ndm, int32_t shape, sp_plan **out) {
+    if (shape == SP_SHAPE_AUTO) {
+        float ms[SP_DEDISP_NUM_SHAPES];
+        const int rc = sp_autotune_dedisperse(freqs_mhz, nchan, tsamp_s, dms, ndm, SP_AUTOTUNE_SAMPLES,
+                                              SP_AUTOTUNE_REPS, ms, &shape, nullptr);
+        if (rc) return rc;
+    }
+    return create_plan(freqs_mhz, nchan, tsamp_s, dms, ndm, shape, out);
+}
+
+extern "C" int sp_dedisp_shape_info(int32_t shape, int32_t *dm_tile, int32_t *time_tile, int32_t *chan_chunk) {
+    if (shape < 0 || shape >= kDedispNumShapes) return SP_EINVAL;
+    if (dm_tile) *dm_tile = kDedispDmPerThread * kDedispShapeCh[shape];
+    if (time_tile) *time_tile = 32 * kDedispShapeSpt[shape];
+    if (chan_chunk) *chan_chunk = kDedispShapeCh[shape];
+    return SP_OK;
+}
+
+extern "C" int sp_plan_shape(const sp_plan *p, int32_t *shape, int32_t *ntiles, int32_t *smem_bytes) {
+    if (!p) return SP_EINVAL;
+    if (shape) *shape = p->shape;
+    if (ntiles) *ntiles = p->ntiles;
+    if (smem_bytes) *smem_bytes = p->smem_bytes;
     return SP_OK;
 }
 

@@ -28,6 +28,7 @@
 // 8-bit beams of up to 8192 channels always qualify.  A CTA that cannot
 // prove it evaluates the same formula in 64-bit integers instead.
 #include <cmath>
+#include <mutex>
 
 #include "sp_internal.h"
 
@@ -351,6 +352,39 @@ int64_t sps_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm
     return align256((int64_t)ndm * nblk * 4) + align256((int64_t)ndm * nblk * nw * 8);
 }
 
+namespace {
+std::mutex g_sps_lock;
+size_t g_sps_smem[64][2] = {};  // configured boxcar shared memory per (device, kernel)
+
+int configure_boxcar(bool map, size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SP_ECUDA;
+    }
+    if (dev < 0 || dev >= 64) return SP_ELIMIT;
+    std::lock_guard<std::mutex> guard(g_sps_lock);
+    if (g_sps_smem[dev][map] >= smem) return SP_OK;
+    const cudaError_t e = map ? cudaFuncSetAttribute(sps_boxcar_kernel<true>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                              : cudaFuncSetAttribute(sps_boxcar_kernel<false>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SP_ECUDA;
+    }
+    g_sps_smem[dev][map] = smem;
+    return SP_OK;
+}
+}  // namespace
+
+int sps_configure(int32_t maxw) {
+    const size_t smem = boxcar_smem(maxw);
+    int rc = configure_boxcar(false, smem);
+    if (!rc) rc = configure_boxcar(true, smem);
+    return rc;
+}
+
 int launch_sps(const SpsArgs &a, cudaStream_t stream) {
     WidthList wl;
     for (int k = 0; k < SP_MAX_WIDTHS; ++k) wl.w[k] = k < a.nw ? a.widths[k] : 0;
@@ -359,31 +393,20 @@ int launch_sps(const SpsArgs &a, cudaStream_t stream) {
     int32_t *m0s = reinterpret_cast<int32_t *>(a.work);
     float2 *coefs = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(a.work) +
                                                align256((int64_t)a.ndm * a.nblk * 4));
+    const size_t smem = boxcar_smem(maxw);
+    const bool map = a.map_best != nullptr;
+    int rc = configure_boxcar(map, smem);
+    if (rc) return rc;
     sps_stats_kernel<<<dim3((unsigned)a.nblk, (unsigned)a.ndm), 256, 0, stream>>>(a.dmt, a.n_out, a.norm_block,
                                                                                 a.nblk, wl, m0s, coefs);
     if (cudaGetLastError() != cudaSuccess) return SP_ECUDA;
 
-    const size_t smem = boxcar_smem(maxw);
     const dim3 grid((unsigned)((a.n_out + kBxT - 1) / kBxT), (unsigned)((a.ndm + kBxIn - 1) / kBxIn));
-    if (a.map_best) {
-        static size_t configured = 0;
-        if (configured < smem) {
-            if (cudaFuncSetAttribute(sps_boxcar_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
-                return SP_ECUDA;
-            configured = smem;
-        }
+    if (map) {
         sps_boxcar_kernel<true><<<grid, 256, smem, stream>>>(a.dmt, a.ndm, a.n_out, wl, maxw, a.threshold,
                                                              a.norm_block, a.nblk, m0s, coefs, nullptr, 0,
                                                              nullptr, a.map_best, a.map_wbest);
     } else {
-        static size_t configured = 0;
-        if (configured < smem) {
-            if (cudaFuncSetAttribute(sps_boxcar_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
-                return SP_ECUDA;
-            configured = smem;
-        }
         if (cudaMemsetAsync(a.count, 0, sizeof(int64_t), stream) != cudaSuccess) return SP_ECUDA;
         sps_boxcar_kernel<false><<<grid, 256, smem, stream>>>(
             a.dmt, a.ndm, a.n_out, wl, maxw, a.threshold, a.norm_block, a.nblk, m0s, coefs, a.cands, a.cap,

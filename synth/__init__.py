@@ -150,18 +150,11 @@ def draw_bursts(rng: np.random.Generator, nbursts: int, n_out: int, dm_lo: float
     return [Burst(int(t), float(d), float(f), float(s)) for t, d, f, s in zip(t0s, dms, fwhms, snrs)]
 
 
-def make_beam(seed: int, nchan: int, n_in: int, freqs: np.ndarray, bursts: list[Burst] | None = None,
-              widths=(1,), gains: np.ndarray | None = None, tsamp: float = TSAMP,
-              chunk_rows: int = 8192) -> np.ndarray:
-    """uint8 filterbank [n_in][nchan] (time-major, channel 0 = highest
-    frequency): x = clip(round(g_c * (128 + 16 z + signal)), 0, 255).  Burst
-    amplitudes are filled in (``Burst.amp``) from their target S/N."""
-    rng = np.random.default_rng(seed)
-    freqs = np.asarray(freqs, dtype=np.float64)
-    g = np.ones(nchan, np.float64) if gains is None else np.asarray(gains, np.float64)
-    bursts = list(bursts or [])
-    # Sparse signal: for each burst a band of samples around each channel's
-    # arrival time.
+def _burst_signal(bursts: list[Burst], freqs: np.ndarray, n_in: int, widths, g: np.ndarray, tsamp: float):
+    """Sparse signal of the bursts: (rows, cols, values) sorted by row, for
+    a band of samples around each channel's arrival time.  Fills in each
+    burst's amplitude from its target S/N."""
+    nchan = freqs.size
     sig_rows, sig_cols, sig_vals = [], [], []
     for b in bursts:
         b.amp = burst_amplitude(b.snr, b.fwhm, widths, g)
@@ -178,9 +171,21 @@ def make_beam(seed: int, nchan: int, n_in: int, freqs: np.ndarray, bursts: list[
     if sig_rows:
         sr = np.concatenate(sig_rows); sc = np.concatenate(sig_cols); sv = np.concatenate(sig_vals)
         order = np.argsort(sr, kind="stable")
-        sr, sc, sv = sr[order], sc[order], sv[order]
-    else:
-        sr = np.zeros(0, np.int64); sc = sr; sv = np.zeros(0)
+        return sr[order], sc[order], sv[order]
+    z = np.zeros(0, np.int64)
+    return z, z, np.zeros(0)
+
+
+def make_beam(seed: int, nchan: int, n_in: int, freqs: np.ndarray, bursts: list[Burst] | None = None,
+              widths=(1,), gains: np.ndarray | None = None, tsamp: float = TSAMP,
+              chunk_rows: int = 8192) -> np.ndarray:
+    """uint8 filterbank [n_in][nchan] (time-major, channel 0 = highest
+    frequency): x = clip(round(g_c * (128 + 16 z + signal)), 0, 255).  Burst
+    amplitudes are filled in (``Burst.amp``) from their target S/N."""
+    rng = np.random.default_rng(seed)
+    freqs = np.asarray(freqs, dtype=np.float64)
+    g = np.ones(nchan, np.float64) if gains is None else np.asarray(gains, np.float64)
+    sr, sc, sv = _burst_signal(list(bursts or []), freqs, n_in, widths, g, tsamp)
 
     out = np.empty((n_in, nchan), dtype=np.uint8)
     gf = g.astype(np.float32)
@@ -196,6 +201,37 @@ def make_beam(seed: int, nchan: int, n_in: int, freqs: np.ndarray, bursts: list[
         np.rint(v, out=v)
         np.clip(v, 0, 255, out=v)
         out[r0:r1] = v.astype(np.uint8)
+    return out
+
+
+def make_beam_torch(seed: int, out, freqs: np.ndarray, bursts: list[Burst] | None = None, widths=(1,),
+                    gains: np.ndarray | None = None, tsamp: float = TSAMP, chunk_rows: int = 16384):
+    """The noise model of ``make_beam`` drawn on a torch device (for beams
+    too large to draw on the host in reasonable time): fills ``out``, a
+    uint8 tensor [n_in][nchan], in place.  Same distribution and burst
+    model; a different random stream (torch's generator, seeded by
+    ``seed``)."""
+    import torch
+    n_in, nchan = int(out.shape[0]), int(out.shape[1])
+    dev = out.device
+    freqs = np.asarray(freqs, dtype=np.float64)
+    g = np.ones(nchan, np.float64) if gains is None else np.asarray(gains, np.float64)
+    sr, sc, sv = _burst_signal(list(bursts or []), freqs, n_in, widths, g, tsamp)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    gt = torch.as_tensor(g.astype(np.float32), device=dev)
+    for r0 in range(0, n_in, chunk_rows):
+        r1 = min(n_in, r0 + chunk_rows)
+        v = torch.randn((r1 - r0, nchan), generator=gen, device=dev, dtype=torch.float32)
+        v.mul_(NOISE_STD).add_(NOISE_MEAN)
+        lo, hi = np.searchsorted(sr, r0), np.searchsorted(sr, r1)
+        if hi > lo:
+            idx = (torch.as_tensor(sr[lo:hi] - r0, device=dev), torch.as_tensor(sc[lo:hi], device=dev))
+            v.index_put_(idx, torch.as_tensor(sv[lo:hi].astype(np.float32), device=dev), accumulate=True)
+        if gains is not None:
+            v.mul_(gt[None, :])
+        v.round_().clamp_(0, 255)
+        out[r0:r1].copy_(v.to(torch.uint8))
     return out
 
 
@@ -242,3 +278,58 @@ def make_workload_beam(wl: Workload, n_in: int, seed: int | None = None):
                          wl.fwhm_hi, wl.snr_lo, wl.snr_hi)
     data = make_beam(s, wl.nchan, n_in, wl.freqs, bursts, widths=wl.widths, tsamp=wl.tsamp)
     return data, bursts
+
+
+@dataclasses.dataclass
+class BatchWorkload:
+    """Many beams of uneven length and DM range searched as one batch."""
+    name: str
+    nchan: int
+    freqs: np.ndarray
+    plan_dms: list            # DM list per plan
+    beam_plan: np.ndarray     # int32 [nbeams] plan index
+    n_out: np.ndarray         # int64 [nbeams]
+    widths: np.ndarray
+    threshold: float
+    norm_block: int
+    seed: int
+    nbursts: int              # per beam
+    fwhm_lo: float = 1.0
+    fwhm_hi: float = 16.0
+    snr_lo: float = 8.0
+    snr_hi: float = 30.0
+    tsamp: float = TSAMP
+
+    @property
+    def nbeams(self) -> int:
+        return int(self.n_out.size)
+
+    def beam_seed(self, b: int) -> int:
+        return int(np.random.SeedSequence((self.seed, int(b))).generate_state(1)[0])
+
+    def gains(self, b: int) -> np.ndarray:
+        """Bandpass gain of beam b: U(0.5, 1.5) per channel."""
+        return np.random.default_rng((self.seed, int(b), 2)).uniform(0.5, 1.5, self.nchan)
+
+    def bursts(self, b: int) -> list[Burst]:
+        """Bursts of beam b: DM U(50, max DM - 50) of its plan, FWHM, S/N and
+        spacing as in the single-beam workloads."""
+        brng = np.random.default_rng((self.seed, int(b), 1))
+        hi = float(self.plan_dms[int(self.beam_plan[b])][-1]) - 50.0
+        return draw_bursts(brng, self.nbursts, int(self.n_out[b]), 50.0, hi, self.fwhm_lo, self.fwhm_hi,
+                           self.snr_lo, self.snr_hi)
+
+
+def config3(nbeams: int = 128, n_lo: int = 16384, n_hi: int = 131072, nchan: int = 4096,
+            max_dms=(500.0, 1000.0, 2000.0)) -> BatchWorkload:
+    """Batched: 128 beams of 4096 ch, lengths U{16384..131072}, max DM per
+    beam from {500, 1000, 2000} (the config-2 step schedule cut there),
+    per-channel gains U(0.5, 1.5), 4 bursts per beam, widths 1..256."""
+    rng = np.random.default_rng(1003)
+    n_out = rng.integers(n_lo, n_hi + 1, size=nbeams).astype(np.int64)
+    beam_plan = rng.integers(0, len(max_dms), size=nbeams).astype(np.int32)
+    plan_dms = [dm_plan_upto(m) for m in max_dms]
+    return BatchWorkload(f"{nbeams} beams x {nchan}ch, n_out U{{{n_lo}..{n_hi}}}, max DM in "
+                         f"{{{', '.join(str(int(m)) for m in max_dms)}}}, gains U(0.5,1.5), widths 1-256",
+                         nchan, band_freqs(nchan), plan_dms, beam_plan, n_out, widths_pow2(256), 6.0, 8192,
+                         1003, 4)

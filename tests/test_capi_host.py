@@ -84,3 +84,44 @@ def test_host_delays_odd_plans(lib):
         dms = rng.uniform(0, 3000, 37)  # unsorted
         got, md = sp.compute_delays(f, 6.4e-5, dms)
         assert np.array_equal(got, oracle.delays(f, 6.4e-5, dms))
+
+
+def test_shape_table_and_batch_argument_checks(lib):
+    """Kernel shapes are reported without a GPU; the batch and autotuner
+    entry points reject bad arguments before touching a device."""
+    dt, tt, cc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    seen = set()
+    for s in range(sp.SP_DEDISP_NUM_SHAPES):
+        assert lib.sp_dedisp_shape_info(s, ctypes.byref(dt), ctypes.byref(tt), ctypes.byref(cc)) == sp.SP_OK
+        assert dt.value == 4 * cc.value and tt.value % 128 == 0 and cc.value % 4 == 0
+        seen.add((dt.value, tt.value, cc.value))
+    assert len(seen) == sp.SP_DEDISP_NUM_SHAPES
+    assert (32, 512, 8) in seen
+    assert lib.sp_dedisp_shape_info(sp.SP_DEDISP_NUM_SHAPES, None, None, None) == sp.SP_EINVAL
+    assert lib.sp_dedisp_shape_info(-1, None, None, None) == sp.SP_EINVAL
+    f = synth.band_freqs(8)
+    d = np.array([0.0, 10.0])
+    ms = np.zeros(sp.SP_DEDISP_NUM_SHAPES, np.float32)
+    best = ctypes.c_int32()
+    assert lib.sp_autotune_dedisperse(None, 8, 1e-3, d.ctypes.data, 2, 100, 1, ms.ctypes.data, ctypes.byref(best),
+                                      None) == sp.SP_EINVAL
+    assert lib.sp_autotune_dedisperse(f.ctypes.data, 8, 1e-3, d.ctypes.data, 2, 0, 1, ms.ctypes.data,
+                                      ctypes.byref(best), None) == sp.SP_EINVAL
+    h = ctypes.c_void_p()
+    assert lib.sp_plan_create_shaped(f.ctypes.data, 8, 1e-3, d.ctypes.data, 2, 7, ctypes.byref(h)) == sp.SP_EINVAL
+    assert lib.sp_dedisperse_batch_workspace_bytes(0) == -1
+    assert lib.sp_dedisperse_batch_workspace_bytes(3) % 256 == 0
+    assert lib.sp_dedisperse_batch(None, 1, None, 0, None) == sp.SP_EINVAL
+    w = np.array([1, 2, 4], np.int32)
+    bp = np.zeros(1, np.int32)
+    bn = np.full(1, 100, np.int64)
+    assert lib.sp_batch_create(None, 1, bp.ctypes.data, bn.ctypes.data, 1, w.ctypes.data, 3, 6.0, 0, 10, 1 << 20,
+                               ctypes.byref(h)) == sp.SP_EINVAL
+    assert lib.sp_batch_create(None, 0, None, None, 0, w.ctypes.data, 3, 6.0, 0, 10, 1 << 20, None) == sp.SP_EINVAL
+    for fn, args in [("sp_batch_destroy", [None]), ("sp_batch_info", [None, None, None]),
+                     ("sp_batch_input", [None, 0, None, None]), ("sp_batch_run", [None, 0, None]),
+                     ("sp_batch_capture", [None, 0, None]), ("sp_batch_launch", [None, None]),
+                     ("sp_batch_results", [None, 0, None, 0, None, None]), ("sp_batch_dmt", [None, 0, None]),
+                     ("sp_batch_run_host", [None, None, None, 0, None, None]),
+                     ("sp_batch_status", [None, None, 0]), ("sp_batch_group_ms", [None, None])]:
+        assert getattr(lib, fn)(*args) == sp.SP_EINVAL, fn

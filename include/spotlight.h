@@ -372,6 +372,79 @@ int sp_batch_run_host(sp_batch *b, const uint8_t *const *h_in, sp_cand *h_cands,
                       int64_t cap_per_beam, int64_t *h_counts, void *stream);
 int sp_batch_status(const sp_batch *b, int32_t *h_status, int32_t clear);
 
+/* ---------------------------------------------------------------- stream --
+ * Real-time streaming search (Sec. 2 and 3.1: each beam arrives as a
+ * continuous stream that is read in blocks overlapping by the largest
+ * dispersion sweep, and each block must be searched before the next one
+ * arrives).  Beam b's samples arrive in order: first max_delay samples of
+ * history (sp_stream_history), then gulps of `gulp` samples
+ * (sp_stream_push).  Gulp k of a beam (k = 0, 1, ...) is searched over
+ * output samples [k*gulp, (k+1)*gulp) of that beam, from the n_in =
+ * gulp + max_delay input samples [k*gulp, k*gulp + n_in): exactly
+ * sp_dedisperse and sp_single_pulse_search of that window (a beam of n_out
+ * = gulp; one normalisation block when gulp <= norm_block).
+ *
+ * Device memory: one ring per beam holding the last n_in samples (uint8,
+ * time-major), then as many in-flight slots (staged window, DM transform,
+ * search scratch, candidates) as fit in hbm_budget_bytes beside the rings,
+ * at most max_batch per launch stream.  SP_ENOMEM if not even one fits.
+ * Scheduling (continuous batching): pushed gulps wait in a FIFO.  Whenever
+ * a launch stream and slots are free, the oldest pending gulps (at most
+ * max_batch) form a batch: each gulp is copied into its ring (after the
+ * beam's previous window was staged), its window is staged into a slot, all
+ * of the batch is dedispersed in one persistent launch, each gulp is
+ * searched and its candidates are copied back.  Two launch streams let a
+ * batch be admitted while the previous one is still on the GPU.  Flags:
+ * SP_STREAM_PER_GULP dedisperses each gulp with its own launch;
+ * SP_STREAM_ONE_STREAM uses a single launch stream (per-gulp launches on
+ * one stream is the per-beam comparison).
+ * All progress happens inside sp_stream_push and sp_stream_poll: there are
+ * no threads, and one host thread must drive a stream object.
+ *
+ * sp_stream_history: copies h_hist [max_delay][nchan] (host) into the beam's
+ *   ring and restarts its gulp count at 0; synchronous; SP_EINVAL while the
+ *   beam has gulps pending or in flight.
+ * sp_stream_push: queues gulp h_gulp [gulp][nchan] (host; page-locked
+ *   memory makes its copy asynchronous) of the beam, stamps its arrival time
+ *   (sp_stream_now's clock) and writes its sequence number to *seq (may be
+ *   NULL); the buffer must stay valid and unchanged until poll has returned
+ *   that gulp's result.  SP_EINVAL before the beam's history.
+ * sp_stream_poll: makes progress, then moves up to max_results finished
+ *   gulps (in completion order) to out[] and their candidates to
+ *   cands + i * cand_cap (cands may be NULL); *n_results = how many.  wait
+ *   != 0 blocks until at least one result is ready or nothing is in flight.
+ * sp_gulp_result: beam, seq, t0 = seq * gulp (first searched sample of the
+ *   window in the beam's output time), count (total candidates; only
+ *   min(count, cand_cap) are returned; status SP_EOVERFLOW when it exceeds),
+ *   t_push and t_done (host seconds: arrival, and when the gulp's results
+ *   were on the host).
+ * sp_stream_pending: gulps queued, in flight and finished-but-not-polled.
+ * sp_stream_info: slot count, device bytes held, window length n_in.
+ * sp_stream_now: the clock of t_push / t_done (seconds, monotonic). */
+typedef struct sp_stream sp_stream;
+typedef struct {
+    int32_t beam;
+    int32_t status;
+    int64_t seq;
+    int64_t t0;
+    int64_t count;
+    double t_push;
+    double t_done;
+} sp_gulp_result;
+#define SP_STREAM_PER_GULP 1
+#define SP_STREAM_ONE_STREAM 2
+int sp_stream_create(const sp_plan *plan, int32_t nbeams, int64_t gulp, const int32_t *h_widths,
+                     int32_t nw, float threshold, int64_t norm_block, int64_t cand_cap,
+                     int64_t hbm_budget_bytes, int32_t max_batch, int32_t flags, sp_stream **out);
+int sp_stream_destroy(sp_stream *s);
+int sp_stream_info(const sp_stream *s, int32_t *slots, int64_t *device_bytes, int64_t *n_in);
+int sp_stream_history(sp_stream *s, int32_t beam, const uint8_t *h_hist);
+int sp_stream_push(sp_stream *s, int32_t beam, const uint8_t *h_gulp, int64_t *seq);
+int sp_stream_poll(sp_stream *s, int32_t wait, sp_gulp_result *out, sp_cand *cands,
+                   int32_t max_results, int32_t *n_results);
+int sp_stream_pending(const sp_stream *s, int64_t *queued, int64_t *in_flight, int64_t *ready);
+double sp_stream_now(void);
+
 #ifdef __cplusplus
 }
 #endif

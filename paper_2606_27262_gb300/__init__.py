@@ -16,6 +16,7 @@ Names mirror the C entry points:
 * ``autotune_dedisperse``        sp_autotune_dedisperse (kernel shape choice)
 * ``dedisperse_batch``           sp_dedisperse_batch (many beams, one launch)
 * ``Batch``                      sp_batch_* (grouped multi-beam step, graph)
+* ``Stream``                     sp_stream_* (real-time gulps, continuous batching)
 """
 from __future__ import annotations
 
@@ -85,6 +86,14 @@ SIGNATURES = {
     "sp_batch_dmt": (ctypes.c_int, [P, I32, P]),
     "sp_batch_run_host": (ctypes.c_int, [P, P, P, I64, P, P]),
     "sp_batch_status": (ctypes.c_int, [P, P, I32]),
+    "sp_stream_create": (ctypes.c_int, [P, I32, I64, P, I32, F32, I64, I64, I64, I32, I32, P]),
+    "sp_stream_destroy": (ctypes.c_int, [P]),
+    "sp_stream_info": (ctypes.c_int, [P, P, P, P]),
+    "sp_stream_history": (ctypes.c_int, [P, I32, P]),
+    "sp_stream_push": (ctypes.c_int, [P, I32, P, P]),
+    "sp_stream_poll": (ctypes.c_int, [P, I32, P, P, I32, P]),
+    "sp_stream_pending": (ctypes.c_int, [P, P, P, P]),
+    "sp_stream_now": (F64, []),
     "sp_probe_iadd3_rate": (ctypes.c_int, [ctypes.c_int, P, P]),
 }
 SP_DEDISP_NUM_SHAPES = 3
@@ -92,6 +101,7 @@ SP_SHAPE_AUTO = -1
 SP_AUTOTUNE_SAMPLES = 16384
 SP_AUTOTUNE_REPS = 3
 SP_BATCH_GROUPED, SP_BATCH_PER_BEAM, SP_BATCH_GROUPED_GRID, SP_BATCH_TIMED = 0, 1, 2, 16
+SP_STREAM_PER_GULP, SP_STREAM_ONE_STREAM = 1, 2
 
 
 def _lib():
@@ -484,6 +494,95 @@ class Batch:
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib().sp_batch_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GulpResult(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int32), ("status", ctypes.c_int32), ("seq", ctypes.c_int64),
+                ("t0", ctypes.c_int64), ("count", ctypes.c_int64), ("t_push", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+def stream_now() -> float:
+    """The clock of the stream's arrival and completion stamps (seconds)."""
+    return float(_lib().sp_stream_now())
+
+
+class Stream:
+    """Real-time streaming search (sp_stream_*): per-beam device rings,
+    HBM-budgeted slots, continuous batching of pushed gulps."""
+
+    def __init__(self, plan: Plan, nbeams: int, gulp: int, widths, threshold: float, norm_block: int,
+                 cand_cap: int, hbm_budget_bytes: int, max_batch: int = 16, flags: int = 0):
+        w = _widths(widths)
+        h = ctypes.c_void_p()
+        _check(_lib().sp_stream_create(plan.handle, int(nbeams), int(gulp), w.ctypes.data, w.size, float(threshold),
+                                       int(norm_block), int(cand_cap), int(hbm_budget_bytes), int(max_batch),
+                                       int(flags), ctypes.byref(h)), "sp_stream_create")
+        self._h = h
+        self.plan, self.nbeams, self.gulp, self.cap = plan, int(nbeams), int(gulp), int(cand_cap)
+        sl, nb, ni = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib().sp_stream_info(h, ctypes.byref(sl), ctypes.byref(nb), ctypes.byref(ni)), "sp_stream_info")
+        self.slots, self.device_bytes, self.n_in = int(sl.value), int(nb.value), int(ni.value)
+        self._keep = {}  # host buffers referenced by gulps not yet returned
+
+    def history(self, beam: int, h_hist):
+        _check(_lib().sp_stream_history(self._h, int(beam), _ptr(h_hist)), "sp_stream_history")
+
+    def push(self, beam: int, h_gulp) -> int:
+        """Queues one gulp (host uint8 [gulp][nchan]); returns its sequence
+        number.  The buffer is kept referenced until its result is polled."""
+        seq = ctypes.c_int64()
+        _check(_lib().sp_stream_push(self._h, int(beam), _ptr(h_gulp), ctypes.byref(seq)), "sp_stream_push")
+        self._keep[(int(beam), int(seq.value))] = h_gulp
+        return int(seq.value)
+
+    def poll(self, wait: bool = False, max_results: int = 64, with_cands: bool = True):
+        """Finished gulps: list of (GulpResult, candidates structured array
+        sorted by (dm_idx, t)) in completion order."""
+        if getattr(self, "_res_n", 0) < max_results:
+            self._res = (GulpResult * max_results)()
+            self._cands = np.zeros((max_results * self.cap, 4), np.int32)
+            self._res_n = max_results
+        res, cands = self._res, self._cands
+        n = ctypes.c_int32()
+        _check(_lib().sp_stream_poll(self._h, int(bool(wait)), ctypes.cast(res, ctypes.c_void_p),
+                                     cands.ctypes.data if with_cands else None, int(max_results), ctypes.byref(n)),
+               "sp_stream_poll")
+        out = []
+        for i in range(n.value):
+            r = res[i]
+            self._keep.pop((int(r.beam), int(r.seq)), None)
+            c = (cands_to_numpy(cands[i * self.cap:(i + 1) * self.cap], min(int(r.count), self.cap))
+                 if with_cands else None)
+            out.append((GulpResult.from_buffer_copy(r), c))
+        return out
+
+    def pending(self):
+        q, f, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib().sp_stream_pending(self._h, ctypes.byref(q), ctypes.byref(f), ctypes.byref(r)),
+               "sp_stream_pending")
+        return int(q.value), int(f.value), int(r.value)
+
+    def drain(self, with_cands: bool = True):
+        """Polls (blocking) until nothing is queued or in flight."""
+        out = []
+        while True:
+            out += self.poll(wait=True, with_cands=with_cands)
+            q, f, r = self.pending()
+            if q == 0 and f == 0 and r == 0:
+                return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().sp_stream_destroy(self._h)
+            self._h = None
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -44,10 +44,12 @@ constexpr int kStTime = 64;
 constexpr int kStChan = 64;
 
 // 64 samples x 64 channels per CTA through shared memory.  Positions of the
-// output at and past n_in (up to the pitch) are written as zeros.
+// output at and past n_in (up to the pitch) are written as zeros.  Sample t
+// is read from input row row0 + t, wrapped at ring_rows (a ring buffer of
+// ring_rows samples; row0 = 0 and ring_rows = n_in for a plain input).
 __global__ void __launch_bounds__(256) stage_input_kernel(const uint8_t *__restrict__ in, int64_t n_in,
                                                           int32_t nchan, uint8_t *__restrict__ xt,
-                                                          int64_t pitch) {
+                                                          int64_t pitch, int64_t row0, int64_t ring_rows) {
     __shared__ __align__(16) uint8_t tile[kStTime][kStChan + 4];
     const int64_t t0 = (int64_t)blockIdx.x * kStTime;
     const int c0 = blockIdx.y * kStChan;
@@ -57,7 +59,9 @@ __global__ void __launch_bounds__(256) stage_input_kernel(const uint8_t *__restr
         const int64_t t = t0 + r;
         uint32_t v[4] = {0u, 0u, 0u, 0u};
         if (t < n_in) {
-            const uint8_t *src = in + t * nchan + c0 + g;
+            int64_t row = row0 + t;  // row0 < ring_rows and t < n_in <= ring_rows: one wrap at most
+            if (row >= ring_rows) row -= ring_rows;
+            const uint8_t *src = in + row * nchan + c0 + g;
             if ((nchan & 15) == 0 && c0 + g + 16 <= nchan) {
                 const uint4 q = __ldg(reinterpret_cast<const uint4 *>(src));
                 v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
@@ -508,9 +512,11 @@ int configure_shape(int shape, int smem_bytes) {
 }  // namespace
 
 int launch_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_staged, int64_t pitch,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, int64_t row0, int64_t ring_rows) {
+    if (ring_rows <= 0) ring_rows = n_in;
+    if (row0 < 0 || row0 >= ring_rows || n_in > ring_rows) return SP_EINVAL;
     const dim3 grid((unsigned)(pitch / kStTime), (unsigned)((nchan + kStChan - 1) / kStChan));
-    stage_input_kernel<<<grid, 256, 0, stream>>>(d_in, n_in, nchan, d_staged, pitch);
+    stage_input_kernel<<<grid, 256, 0, stream>>>(d_in, n_in, nchan, d_staged, pitch, row0, ring_rows);
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

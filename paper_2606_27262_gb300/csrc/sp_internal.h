@@ -84,8 +84,10 @@ int compute_delays(const double *freqs, int32_t nchan, double tsamp, const doubl
                    int32_t ndm, std::vector<int32_t> &out, int32_t *max_delay);
 
 // Kernel launchers (return SP_OK or SP_ECUDA).
+// Sample t comes from input row (row0 + t) mod ring_rows (ring_rows 0 = a
+// plain input of n_in rows).
 int launch_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_staged,
-                       int64_t pitch, cudaStream_t stream);
+                       int64_t pitch, cudaStream_t stream, int64_t row0 = 0, int64_t ring_rows = 0);
 int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, int64_t n_out,
                       int32_t *d_out, cudaStream_t stream);
 // One beam of a batched dedispersion launch, as the kernel reads it.

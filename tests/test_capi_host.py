@@ -125,3 +125,21 @@ def test_shape_table_and_batch_argument_checks(lib):
                      ("sp_batch_run_host", [None, None, None, 0, None, None]),
                      ("sp_batch_status", [None, None, 0]), ("sp_batch_group_ms", [None, None])]:
         assert getattr(lib, fn)(*args) == sp.SP_EINVAL, fn
+
+
+def test_stream_argument_checks(lib):
+    """The streaming entry points reject bad arguments before any device
+    work; the clock is monotonic."""
+    w = np.array([1, 2, 4], np.int32)
+    h = ctypes.c_void_p()
+    assert lib.sp_stream_create(None, 4, 100, w.ctypes.data, 3, 6.0, 0, 16, 1 << 30, 4, 0, ctypes.byref(h)) \
+        == sp.SP_EINVAL
+    assert lib.sp_stream_create(None, 4, 100, w.ctypes.data, 3, 6.0, 0, 16, 1 << 30, 4, 0, None) == sp.SP_EINVAL
+    for fn, args in [("sp_stream_destroy", [None]), ("sp_stream_info", [None, None, None, None]),
+                     ("sp_stream_history", [None, 0, None]), ("sp_stream_push", [None, 0, None, None]),
+                     ("sp_stream_poll", [None, 0, None, None, 0, None]),
+                     ("sp_stream_pending", [None, None, None, None])]:
+        assert getattr(lib, fn)(*args) == sp.SP_EINVAL, fn
+    t0 = lib.sp_stream_now()
+    t1 = lib.sp_stream_now()
+    assert t1 >= t0 > 0

@@ -372,6 +372,40 @@ int sp_batch_run_host(sp_batch *b, const uint8_t *const *h_in, sp_cand *h_cands,
                       int64_t cap_per_beam, int64_t *h_counts, void *stream);
 int sp_batch_status(const sp_batch *b, int32_t *h_status, int32_t clear);
 
+/* ----------------------------------------------------------------- sifter --
+ * Candidate sifting after the single-pulse search (Sec. 3.2.1), host code:
+ * DBSCAN clustering of one beam's candidates in the DM-time plane, the
+ * highest-S/N member of each cluster kept, then thresholds.  Coordinates
+ * are the trial DM in pc cm^-3 (h_dms[dm_idx]) and the arrival time in
+ * seconds (t * tsamp_s); two candidates are neighbours when their Euclidean
+ * distance is at most eps; a core candidate has at least min_points
+ * neighbours (itself included); clusters grow breadth first from the first
+ * unclustered core candidate in (dm_idx, t) order, and a border candidate
+ * near two clusters joins the one that reaches it first.  Candidates in no
+ * cluster are dropped.  A cluster's peak (highest S/N, first in (dm_idx, t)
+ * order on ties) is kept when snr >= snr_min, DM >= dm_min and width
+ * (h_widths[width_idx] * tsamp_s) <= width_max_s.
+ *   h_cands [n]        host candidates (any order).
+ *   h_dms [ndm], h_widths [nw]  the search's trial DMs and widths (samples).
+ *   h_out [cap]        receives the kept peaks in (dm_idx, t) order;
+ *   *n_out             how many were kept (SP_EOVERFLOW if more than cap).
+ *   h_labels [n]       optional (NULL): cluster id of each input candidate
+ *                      (clusters numbered in discovery order), -1 for noise.
+ * SP_SIFT_DEFAULTS are the values of Sec. 3.2.1: eps 0.5, 5 points,
+ * S/N 10, DM 10 pc cm^-3, width 100 ms.  Synchronous; touches no GPU.
+ * Errors: SP_EINVAL (bad arguments or a candidate index out of range). */
+typedef struct {
+    float eps;
+    int32_t min_points;
+    float snr_min;
+    float dm_min;
+    float width_max_s;
+} sp_sift_params;
+#define SP_SIFT_DEFAULTS {0.5f, 5, 10.0f, 10.0f, 0.1f}
+int sp_sift(const sp_cand *h_cands, int64_t n, const double *h_dms, int32_t ndm,
+            const int32_t *h_widths, int32_t nw, double tsamp_s, const sp_sift_params *params,
+            sp_cand *h_out, int64_t cap, int64_t *n_out, int32_t *h_labels);
+
 /* ---------------------------------------------------------------- stream --
  * Real-time streaming search (Sec. 2 and 3.1: each beam arrives as a
  * continuous stream that is read in blocks overlapping by the largest

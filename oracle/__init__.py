@@ -12,6 +12,7 @@ shares no code with the CUDA library (``paper_2606_27262_gb300``): the C file
 * ``boxcar_snr``    Sec. 3.1.2, boxcar matched filter via the cumulative sum.
 * ``best``          Sec. 3.1.2, best S/N over the trial widths.
 * ``peaks``         Sec. 3.1.2, 3x3 peak filter in the DM-time plane + threshold.
+* ``sift.sift``     Sec. 3.2.1, DBSCAN clustering, cluster peaks, thresholds (numpy).
 
 The shared library is compiled from ``oracle.c`` with gcc on first use
 (``-O2 -ffp-contract=off -fopenmp``) into ``oracle/_build/``.

@@ -17,6 +17,7 @@ Names mirror the C entry points:
 * ``dedisperse_batch``           sp_dedisperse_batch (many beams, one launch)
 * ``Batch``                      sp_batch_* (grouped multi-beam step, graph)
 * ``Stream``                     sp_stream_* (real-time gulps, continuous batching)
+* ``sift``                       sp_sift (DBSCAN clustering + thresholds, host)
 """
 from __future__ import annotations
 
@@ -94,6 +95,7 @@ SIGNATURES = {
     "sp_stream_poll": (ctypes.c_int, [P, I32, P, P, I32, P]),
     "sp_stream_pending": (ctypes.c_int, [P, P, P, P]),
     "sp_stream_now": (F64, []),
+    "sp_sift": (ctypes.c_int, [P, I64, P, I32, P, I32, F64, P, P, I64, P, P]),
     "sp_probe_iadd3_rate": (ctypes.c_int, [ctypes.c_int, P, P]),
 }
 SP_DEDISP_NUM_SHAPES = 3
@@ -589,6 +591,35 @@ class Stream:
             self.close()
         except Exception:
             pass
+
+
+class SiftParams(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_float), ("min_points", ctypes.c_int32), ("snr_min", ctypes.c_float),
+                ("dm_min", ctypes.c_float), ("width_max_s", ctypes.c_float)]
+
+
+SIFT_DEFAULTS = dict(eps=0.5, min_points=5, snr_min=10.0, dm_min=10.0, width_max_s=0.1)
+
+
+def sift(cands: np.ndarray, dms, widths, tsamp: float, labels: bool = False, **params):
+    """sp_sift on a structured candidate array (CAND_DTYPE).  Returns the
+    kept cluster peaks sorted by (dm_idx, t), and the per-candidate cluster
+    labels when ``labels``."""
+    p = dict(SIFT_DEFAULTS)
+    p.update(params)
+    c = np.ascontiguousarray(cands, dtype=CAND_DTYPE)
+    d = np.ascontiguousarray(dms, dtype=np.float64)
+    w = _widths(widths)
+    out = np.zeros(max(c.size, 1), CAND_DTYPE)
+    lab = np.zeros(max(c.size, 1), np.int32)
+    n = ctypes.c_int64()
+    sp_p = SiftParams(float(p["eps"]), int(p["min_points"]), float(p["snr_min"]), float(p["dm_min"]),
+                      float(p["width_max_s"]))
+    _check(_lib().sp_sift(c.ctypes.data if c.size else None, c.size, d.ctypes.data, d.size, w.ctypes.data, w.size,
+                          float(tsamp), ctypes.byref(sp_p), out.ctypes.data, out.size, ctypes.byref(n),
+                          lab.ctypes.data if labels else None), "sp_sift")
+    kept = out[:n.value].copy()
+    return (kept, lab[:c.size].copy()) if labels else kept
 
 
 def probe_iadd3_rate(iters: int = 4096):

@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *ARCH, "-
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math"]
 
 CUDA_SOURCES = ["dedisperse.cu", "sps.cu", "sps_noalloc.cu", "probe.cu"]
-CXX_SOURCES = ["plan.cpp", "capi.cpp", "autotune.cpp", "batch.cpp", "stream.cpp"]
+CXX_SOURCES = ["plan.cpp", "capi.cpp", "autotune.cpp", "batch.cpp", "stream.cpp", "sifter.cpp"]
 
 
 def cuda_home() -> str:

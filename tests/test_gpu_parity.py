@@ -290,3 +290,21 @@ def test_staged_entry_points():
     rate, nsm = sp.probe_iadd3_rate(256)
     assert nsm >= 100 and 16 <= rate <= 160
     assert plan.status() == 0
+
+
+def test_config2_sift(config2_run):
+    """Sifting the GPU's config-2 candidates (Sec. 3.2.1): the library's
+    sifter equals the oracle sifter on the same list, and the injected
+    bursts the search found at S/N >= 12 keep a cluster peak nearby."""
+    from oracle import sift as osift
+    wl, plan, x, bursts, dmt = config2_run
+    g, gn = gu.dev_candidates(dmt, wl.widths, wl.threshold, wl.norm_block, cap=1 << 22)
+    got, glab = sp.sift(g, wl.dms, wl.widths, wl.tsamp, labels=True)
+    want, wlab = osift.sift(g, wl.dms, wl.widths, wl.tsamp)
+    assert np.array_equal(glab, wlab) and np.array_equal(got, want)
+    assert 0 < got.size < g.size
+    for b in bursts:
+        seen = g[(np.abs(wl.dms[g["dm_idx"]] - b.dm) <= 5) & (np.abs(g["t"] - b.t0) <= 64) & (g["snr"] >= 12)]
+        if seen.size >= 5:
+            near = (np.abs(wl.dms[got["dm_idx"]] - b.dm) <= 10) & (np.abs(got["t"] - b.t0) <= 400)
+            assert near.any(), b

@@ -406,6 +406,69 @@ int sp_sift(const sp_cand *h_cands, int64_t n, const double *h_dms, int32_t ndm,
             const int32_t *h_widths, int32_t nw, double tsamp_s, const sp_sift_params *params,
             sp_cand *h_out, int64_t cap, int64_t *n_out, int32_t *h_labels);
 
+/* ------------------------------------------------------------ classifier --
+ * Candidate classifier (Sec. 3.2.2: a convolutional network scores each
+ * sifted candidate from two images -- its dynamic spectrum dedispersed at
+ * the candidate DM and its DM transform over a narrow DM range -- with one
+ * network per image fused multiplicatively into one probability; candidates
+ * pass at p >= 0.5).  The paper's pretrained networks are not available;
+ * this one is trained by the library's own kernels.
+ *
+ * Images: bf16 [batch][256][256] (rows = subbands or DM offsets, columns =
+ * time bins), device, 16-byte aligned.  sp_cnn_features makes both from
+ * subband dynamic spectra d_sub fp32 [batch][nsub = 256][t_in] that are
+ * already dedispersed at the candidate DM within each subband: the
+ * frequency-time image is the centre 256 bins, u0 = (t_in - 256) / 2, and
+ * DM-time row j is sum_s d_sub[s][u0 + u + shift[j][s]] (out-of-range bins
+ * count 0), shift from sp_dmt_shifts; each image is then scaled to zero
+ * mean and unit variance.  d_work: sp_cnn_features_workspace_bytes(batch)
+ * bytes, 256-byte aligned.
+ * sp_dmt_shifts: h_shift [256][nsub] for a band freqs_mhz [nchan] (strictly
+ *   decreasing, nchan a multiple of nsub): row j is a residual dispersion
+ *   sweep of max_sweep * (2j/255 - 1) time bins across the band, i.e.
+ *   shift[j][s] = round(sweep_j * (f_s^-2 - f_0^-2) / (f_last^-2 - f_0^-2))
+ *   with f_s the mean frequency of subband s (Eq. 1 in time bins).
+ *   t_in = 256 + 2 * max_sweep keeps every shifted bin inside d_sub.
+ * Network (per image): five 3x3 convolutions, stride 2, padding 1, with
+ *   1->16->32->64->128->256 channels and ReLU; global average pooling; a
+ *   linear head to one logit l; p = sigmoid(l_ft) * sigmoid(l_dmt).  bf16
+ *   activations and GEMM operands, fp32 accumulation (tensor cores), fp32
+ *   master weights.  Training minimises the binary cross-entropy of p
+ *   (mean over the batch) with Adam (beta 0.9 / 0.999, eps 1e-8).
+ * sp_cnn_create: He-normal weights from `seed`, batch <= max_batch <=
+ *   SP_CNN_MAX_BATCH; allocates all buffers.
+ * sp_cnn_num_params: length of the flat fp32 parameter vector: per image
+ *   (frequency-time first) and per layer W [Cout][9 Cin] (k = (ky*3 +
+ *   kx)*Cin + c) then b [Cout], then the head w [256] and b [1].
+ * sp_cnn_get_params / _set_params / _get_grads: that vector (host); grads
+ *   are those of the last sp_cnn_backward (SP_EINVAL before one).
+ * sp_cnn_forward: d_prob [batch] fp32 device.  sp_cnn_backward: forward with
+ *   d_labels [batch] (1 = astrophysical, 0 = not), gradients, and the loss
+ *   in *h_loss (synchronises; NULL = no copy).  sp_cnn_adam_step applies the
+ *   stored gradients; sp_cnn_train_step = backward + adam step.
+ * Errors: SP_EINVAL, SP_ENOMEM, SP_EWORKSPACE, SP_ECUDA. */
+typedef struct sp_cnn sp_cnn;
+#define SP_CNN_MAX_BATCH 256
+int64_t sp_cnn_num_params(void);
+int sp_cnn_create(int32_t max_batch, uint64_t seed, sp_cnn **out);
+int sp_cnn_destroy(sp_cnn *c);
+int sp_cnn_get_params(const sp_cnn *c, float *h_params);
+int sp_cnn_set_params(sp_cnn *c, const float *h_params);
+int sp_cnn_get_grads(const sp_cnn *c, float *h_grads);
+int sp_cnn_forward(sp_cnn *c, const void *d_ft, const void *d_dmt, int32_t batch, float *d_prob,
+                   void *stream);
+int sp_cnn_backward(sp_cnn *c, const void *d_ft, const void *d_dmt, const float *d_labels,
+                    int32_t batch, float *h_loss, void *stream);
+int sp_cnn_adam_step(sp_cnn *c, float lr, void *stream);
+int sp_cnn_train_step(sp_cnn *c, const void *d_ft, const void *d_dmt, const float *d_labels,
+                      int32_t batch, float lr, float *h_loss, void *stream);
+int64_t sp_cnn_features_workspace_bytes(int32_t batch);
+int sp_cnn_features(const float *d_sub, int32_t batch, int32_t nsub, int32_t t_in,
+                    const int32_t *d_shift, void *d_ft, void *d_dmt, void *d_work,
+                    int64_t work_bytes, void *stream);
+int sp_dmt_shifts(const double *freqs_mhz, int32_t nchan, int32_t nsub, int32_t max_sweep,
+                  int32_t *h_shift);
+
 /* ---------------------------------------------------------------- stream --
  * Real-time streaming search (Sec. 2 and 3.1: each beam arrives as a
  * continuous stream that is read in blocks overlapping by the largest

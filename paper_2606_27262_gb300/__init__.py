@@ -18,6 +18,7 @@ Names mirror the C entry points:
 * ``Batch``                      sp_batch_* (grouped multi-beam step, graph)
 * ``Stream``                     sp_stream_* (real-time gulps, continuous batching)
 * ``sift``                       sp_sift (DBSCAN clustering + thresholds, host)
+* ``Classifier``, ``cnn_features``, ``dmt_shifts``  sp_cnn_* (two-image CNN)
 """
 from __future__ import annotations
 
@@ -96,6 +97,19 @@ SIGNATURES = {
     "sp_stream_pending": (ctypes.c_int, [P, P, P, P]),
     "sp_stream_now": (F64, []),
     "sp_sift": (ctypes.c_int, [P, I64, P, I32, P, I32, F64, P, P, I64, P, P]),
+    "sp_cnn_num_params": (I64, []),
+    "sp_cnn_create": (ctypes.c_int, [I32, ctypes.c_uint64, P]),
+    "sp_cnn_destroy": (ctypes.c_int, [P]),
+    "sp_cnn_get_params": (ctypes.c_int, [P, P]),
+    "sp_cnn_set_params": (ctypes.c_int, [P, P]),
+    "sp_cnn_get_grads": (ctypes.c_int, [P, P]),
+    "sp_cnn_forward": (ctypes.c_int, [P, P, P, I32, P, P]),
+    "sp_cnn_backward": (ctypes.c_int, [P, P, P, P, I32, P, P]),
+    "sp_cnn_adam_step": (ctypes.c_int, [P, F32, P]),
+    "sp_cnn_train_step": (ctypes.c_int, [P, P, P, P, I32, F32, P, P]),
+    "sp_cnn_features_workspace_bytes": (I64, [I32]),
+    "sp_cnn_features": (ctypes.c_int, [P, I32, I32, I32, P, P, P, P, I64, P]),
+    "sp_dmt_shifts": (ctypes.c_int, [P, I32, I32, I32, P]),
     "sp_probe_iadd3_rate": (ctypes.c_int, [ctypes.c_int, P, P]),
 }
 SP_DEDISP_NUM_SHAPES = 3
@@ -104,6 +118,8 @@ SP_AUTOTUNE_SAMPLES = 16384
 SP_AUTOTUNE_REPS = 3
 SP_BATCH_GROUPED, SP_BATCH_PER_BEAM, SP_BATCH_GROUPED_GRID, SP_BATCH_TIMED = 0, 1, 2, 16
 SP_STREAM_PER_GULP, SP_STREAM_ONE_STREAM = 1, 2
+SP_CNN_MAX_BATCH = 256
+CNN_IMG = 256
 
 
 def _lib():
@@ -620,6 +636,82 @@ def sift(cands: np.ndarray, dms, widths, tsamp: float, labels: bool = False, **p
                           lab.ctypes.data if labels else None), "sp_sift")
     kept = out[:n.value].copy()
     return (kept, lab[:c.size].copy()) if labels else kept
+
+
+def dmt_shifts(freqs_mhz, nsub: int = CNN_IMG, max_sweep: int = 128) -> np.ndarray:
+    """int32 [256][nsub] subband shifts of the DM-time image (sp_dmt_shifts)."""
+    f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+    out = np.zeros((CNN_IMG, nsub), np.int32)
+    _check(_lib().sp_dmt_shifts(f.ctypes.data, f.size, int(nsub), int(max_sweep), out.ctypes.data), "sp_dmt_shifts")
+    return out
+
+
+def cnn_features(d_sub, d_shift, d_ft, d_dmt, d_work=None, stream=None):
+    """Frequency-time and DM-time images (bf16 [B][256][256] CUDA tensors)
+    of subband dynamic spectra d_sub float32 [B][256][t_in]."""
+    import torch
+    B, S, T = (int(x) for x in d_sub.shape)
+    if d_work is None:
+        d_work = torch.empty(int(_lib().sp_cnn_features_workspace_bytes(B)), dtype=torch.uint8, device=d_sub.device)
+    _check(_lib().sp_cnn_features(_ptr(d_sub), B, S, T, _ptr(d_shift), _ptr(d_ft), _ptr(d_dmt), _ptr(d_work),
+                                  int(d_work.numel()), _stream(stream)), "sp_cnn_features")
+
+
+class Classifier:
+    """The two-image CNN (sp_cnn_*): forward, backward, Adam on the GPU."""
+
+    def __init__(self, max_batch: int = 64, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib().sp_cnn_create(int(max_batch), int(seed), ctypes.byref(h)), "sp_cnn_create")
+        self._h = h
+        self.max_batch = int(max_batch)
+        self.num_params = int(_lib().sp_cnn_num_params())
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.num_params, np.float32)
+        _check(_lib().sp_cnn_get_params(self._h, out.ctypes.data), "sp_cnn_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.num_params
+        _check(_lib().sp_cnn_set_params(self._h, p.ctypes.data), "sp_cnn_set_params")
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.num_params, np.float32)
+        _check(_lib().sp_cnn_get_grads(self._h, out.ctypes.data), "sp_cnn_get_grads")
+        return out
+
+    def forward(self, d_ft, d_dmt, d_prob, stream=None):
+        _check(_lib().sp_cnn_forward(self._h, _ptr(d_ft), _ptr(d_dmt), int(d_ft.shape[0]), _ptr(d_prob),
+                                     _stream(stream)), "sp_cnn_forward")
+
+    def backward(self, d_ft, d_dmt, d_labels, stream=None) -> float:
+        loss = ctypes.c_float()
+        _check(_lib().sp_cnn_backward(self._h, _ptr(d_ft), _ptr(d_dmt), _ptr(d_labels), int(d_ft.shape[0]),
+                                      ctypes.byref(loss), _stream(stream)), "sp_cnn_backward")
+        return float(loss.value)
+
+    def adam_step(self, lr: float, stream=None):
+        _check(_lib().sp_cnn_adam_step(self._h, float(lr), _stream(stream)), "sp_cnn_adam_step")
+
+    def train_step(self, d_ft, d_dmt, d_labels, lr: float, want_loss: bool = False, stream=None):
+        loss = ctypes.c_float()
+        _check(_lib().sp_cnn_train_step(self._h, _ptr(d_ft), _ptr(d_dmt), _ptr(d_labels), int(d_ft.shape[0]),
+                                        float(lr), ctypes.byref(loss) if want_loss else None, _stream(stream)),
+               "sp_cnn_train_step")
+        return float(loss.value) if want_loss else None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().sp_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def probe_iadd3_rate(iters: int = 4096):

@@ -1,0 +1,491 @@
+// cnn.cu -- kernels of the candidate classifier (arXiv 2606.27262,
+// Sec. 3.2.2: a CNN judges each sifted candidate from two images, its
+// dedispersed dynamic spectrum and its DM transform; two networks, one per
+// image, fused multiplicatively into one probability).
+//
+// Every layer is built from these kernels:
+//   gemm_nt_kernel      C[M,N] = A[M,K] * B[N,K]^T, bf16 operands, fp32
+//                       accumulate on the tensor cores (mma.sync m16n8k16),
+//                       cp.async double buffering, optional split-K; the
+//                       epilogue adds a bias and applies ReLU (bf16 out),
+//                       stores fp32, or adds fp32 atomically.
+//   im2col_kernel       3x3 / stride / pad-1 patches of an NHWC bf16 tensor
+//                       as GEMM rows, k = (ky*3 + kx)*C + c, zero padded.
+//   col2im_relu_kernel  the adjoint of im2col (a gather, no atomics) fused
+//                       with the ReLU derivative of the layer below.
+//   transpose_kernel    bf16 [R][C] -> [C][R] (operands of the backward GEMMs).
+//   features_kernel     frequency-time and DM-time images of a subband
+//                       dynamic spectrum, each normalised to zero mean and
+//                       unit variance, as bf16.
+//   plus average pooling, the linear heads, the fused loss and Adam.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "sp_cnn_internal.h"
+
+namespace sp {
+namespace {
+
+constexpr int kBM = 128, kBN = 64, kBK = 32, kPad = 8;
+constexpr int kLds = kBK + kPad;  // smem row stride (bf16): 80 bytes, conflict-free ldmatrix
+
+__device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    const int n = valid ? 16 : 0;  // zero-fill outside the matrix
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s_addr(dst)), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void ldmatrix_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(s_addr(p)));
+}
+__device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// 256 threads: warp (wm, wn) = (warp % 4, warp / 4) owns a 32 x 32 block of
+// the 128 x 64 tile: 2 x 4 mma tiles of 16 x 8.  blockIdx.z = K split.
+template <int EPI>
+__global__ void __launch_bounds__(256) gemm_nt_kernel(const __nv_bfloat16 *__restrict__ A, int64_t lda,
+                                                      const __nv_bfloat16 *__restrict__ B, int64_t ldb, int M, int N,
+                                                      int64_t K, int64_t k_split, float *__restrict__ Cf,
+                                                      __nv_bfloat16 *__restrict__ Cb, int64_t ldc,
+                                                      const float *__restrict__ bias) {
+    __shared__ __align__(16) __nv_bfloat16 As[2][kBM][kLds];
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][kBN][kLds];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const int64_t m0 = (int64_t)blockIdx.y * kBM, n0 = (int64_t)blockIdx.x * kBN;
+    const int64_t k_lo = (int64_t)blockIdx.z * k_split;
+    const int64_t k_hi = min(K, k_lo + k_split);
+    const int nk = (int)((k_hi - k_lo) / kBK);
+
+    auto load = [&](int kt, int buf) {
+        const int64_t k0 = k_lo + (int64_t)kt * kBK;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {  // A: 128 rows x 4 chunks of 8
+            const int c = tid + i * 256;
+            const int r = c >> 2, q = (c & 3) * 8;
+            const int64_t gr = m0 + r;
+            const bool ok = gr < M;
+            cp_async16(&As[buf][r][q], A + (ok ? gr : 0) * lda + k0 + q, ok);
+        }
+        {  // B: 64 rows x 4 chunks
+            const int r = tid >> 2, q = (tid & 3) * 8;
+            const int64_t gr = n0 + r;
+            const bool ok = gr < N;
+            cp_async16(&Bs[buf][r][q], B + (ok ? gr : 0) * ldb + k0 + q, ok);
+        }
+    };
+
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+    if (nk > 0) {
+        load(0, 0);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < nk) {
+            load(kt + 1, buf ^ 1);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kBK; ks += 16) {
+            uint32_t a[2][4], b[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm * 32 + i * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+                const int c = ks + (lane >> 4) * 8;
+                ldmatrix_x4(a[i][0], a[i][1], a[i][2], a[i][3], &As[buf][r][c]);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                const int r = wn * 32 + jj * 16 + (lane & 7) + (lane >> 4) * 8;
+                const int c = ks + ((lane >> 3) & 1) * 8;
+                ldmatrix_x4(b[2 * jj][0], b[2 * jj][1], b[2 * jj + 1][0], b[2 * jj + 1][1], &Bs[buf][r][c]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j][0], b[j][1]);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t row = m0 + wm * 32 + i * 16 + (lane >> 2) + h * 8;
+                if (row >= M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int64_t col = n0 + wn * 32 + j * 8 + (lane & 3) * 2 + e;
+                    if (col >= N) continue;
+                    float v = acc[i][j][2 * h + e];
+                    if (EPI == kEpiBiasRelu) {
+                        v = fmaxf(v + bias[col], 0.f);
+                        Cb[row * ldc + col] = __float2bfloat16(v);
+                    } else if (EPI == kEpiStore) {
+                        Cf[row * ldc + col] = v;
+                    } else {
+                        atomicAdd(Cf + row * ldc + col, v);
+                    }
+                }
+            }
+}
+
+// cols[p][k] for p = (n, ho, wo), k = (ky*3 + kx)*C + c (k < 9C; zero up to Kp).
+__global__ void im2col_kernel(const __nv_bfloat16 *__restrict__ x, int Nb, int H, int W, int C, int stride, int Ho,
+                              int Wo, int Kp, __nv_bfloat16 *__restrict__ cols) {
+    const int64_t total = (int64_t)Nb * Ho * Wo * Kp;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % Kp);
+        const int64_t p = idx / Kp;
+        __nv_bfloat16 v = __float2bfloat16(0.f);
+        if (k < 9 * C) {
+            const int c = k % C, kk = k / C, ky = kk / 3, kx = kk % 3;
+            const int wo = (int)(p % Wo), ho = (int)((p / Wo) % Ho), n = (int)(p / ((int64_t)Wo * Ho));
+            const int h = ho * stride - 1 + ky, w = wo * stride - 1 + kx;
+            if (h >= 0 && h < H && w >= 0 && w < W) v = x[(((int64_t)n * H + h) * W + w) * C + c];
+        }
+        cols[idx] = v;
+    }
+}
+
+// dz[n][h][w][c] = (sum over the patches that read (h, w) of dcols) *
+// (x[n][h][w][c] > 0): the gradient of im2col's input, masked by the ReLU
+// that produced x.
+__global__ void col2im_relu_kernel(const float *__restrict__ dcols, const __nv_bfloat16 *__restrict__ x, int Nb, int H,
+                                   int W, int C, int stride, int Ho, int Wo, int Kp,
+                                   __nv_bfloat16 *__restrict__ dz) {
+    const int64_t total = (int64_t)Nb * H * W * C;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % C);
+        const int w = (int)((idx / C) % W), h = (int)((idx / ((int64_t)C * W)) % H);
+        const int n = (int)(idx / ((int64_t)C * W * H));
+        float s = 0.f;
+        if (__bfloat162float(x[idx]) > 0.f) {
+            for (int ky = 0; ky < 3; ++ky) {
+                const int hh = h + 1 - ky;
+                if (hh < 0 || hh % stride) continue;
+                const int ho = hh / stride;
+                if (ho >= Ho) continue;
+                for (int kx = 0; kx < 3; ++kx) {
+                    const int ww = w + 1 - kx;
+                    if (ww < 0 || ww % stride) continue;
+                    const int wo = ww / stride;
+                    if (wo >= Wo) continue;
+                    s += dcols[(((int64_t)n * Ho + ho) * Wo + wo) * Kp + (ky * 3 + kx) * C + c];
+                }
+            }
+        }
+        dz[idx] = __float2bfloat16(s);
+    }
+}
+
+__global__ void transpose_kernel(const __nv_bfloat16 *__restrict__ in, int64_t R, int64_t C,
+                                 __nv_bfloat16 *__restrict__ out) {
+    __shared__ __nv_bfloat16 t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;  // rows on x: R can be large
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[i][threadIdx.x] = in[r * C + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[c * R + r] = t[threadIdx.x][i];
+    }
+}
+
+// feat[n][c] = mean over the H*W positions of y[n][.][.][c].
+__global__ void avgpool_kernel(const __nv_bfloat16 *__restrict__ y, int Nb, int HW, int C, float *__restrict__ feat) {
+    const int64_t total = (int64_t)Nb * C;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % C);
+        const int64_t n = idx / C;
+        float s = 0.f;
+        for (int i = 0; i < HW; ++i) s += __bfloat162float(y[(n * HW + i) * C + c]);
+        feat[idx] = s / (float)HW;
+    }
+}
+
+// dz[n][i][c] = dfeat[n][c] / HW * (y > 0): pooling and ReLU backward.
+__global__ void avgpool_back_kernel(const float *__restrict__ dfeat, const __nv_bfloat16 *__restrict__ y, int Nb,
+                                    int HW, int C, __nv_bfloat16 *__restrict__ dz) {
+    const int64_t total = (int64_t)Nb * HW * C;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % C);
+        const int64_t n = idx / ((int64_t)HW * C);
+        const float g = __bfloat162float(y[idx]) > 0.f ? dfeat[n * C + c] / (float)HW : 0.f;
+        dz[idx] = __float2bfloat16(g);
+    }
+}
+
+// logit[n] = feat[n] . w + b, one warp per example.
+__global__ void head_kernel(const float *__restrict__ feat, int Nb, int C, const float *__restrict__ w,
+                            const float *__restrict__ b, float *__restrict__ logit) {
+    const int n = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (n >= Nb) return;
+    float s = 0.f;
+    for (int c = lane; c < C; c += 32) s += feat[(int64_t)n * C + c] * w[c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) logit[n] = s + b[0];
+}
+
+__device__ __forceinline__ float sigmoidf(float x) { return 1.f / (1.f + expf(-x)); }
+
+// Fused probability p = s1 * s2 (s = sigmoid of each branch's logit) and,
+// with labels, the binary cross-entropy of p and its derivative with
+// respect to both logits (mean over the batch).
+__global__ void fuse_loss_kernel(const float *__restrict__ l1, const float *__restrict__ l2,
+                                 const float *__restrict__ label, int Nb, float *__restrict__ prob,
+                                 float *__restrict__ dl1, float *__restrict__ dl2, float *__restrict__ loss) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Nb) return;
+    const float s1 = sigmoidf(l1[n]), s2 = sigmoidf(l2[n]);
+    const float p = s1 * s2;
+    if (prob) prob[n] = p;
+    if (!label) return;
+    const float y = label[n];
+    const float pc = fminf(fmaxf(p, 1e-7f), 1.f - 1e-7f);
+    atomicAdd(loss, -(y * logf(pc) + (1.f - y) * logf(1.f - pc)) / (float)Nb);
+    // dL/dp = (p - y) / (p (1 - p)); dp/dl1 = p (1 - s1); dp/dl2 = p (1 - s2).
+    const float g = (pc - y) / (1.f - pc) / (float)Nb;
+    dl1[n] = g * (1.f - s1);
+    dl2[n] = g * (1.f - s2);
+}
+
+// Head backward: dfeat[n][c] = dl[n] * w[c]; dw[c] += sum_n dl[n] feat[n][c];
+// db += sum_n dl[n].
+__global__ void head_back_kernel(const float *__restrict__ feat, const float *__restrict__ dl, int Nb, int C,
+                                 const float *__restrict__ w, float *__restrict__ dfeat, float *__restrict__ dw,
+                                 float *__restrict__ db) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < C) {
+        float s = 0.f;
+        for (int n = 0; n < Nb; ++n) {
+            s += dl[n] * feat[(int64_t)n * C + c];
+            dfeat[(int64_t)n * C + c] = dl[n] * w[c];
+        }
+        dw[c] += s;
+    }
+    if (c == 0) {
+        float s = 0.f;
+        for (int n = 0; n < Nb; ++n) s += dl[n];
+        db[0] += s;
+    }
+}
+
+// db[c] += sum over rows of dz[.][c] (bias gradient of a conv layer).
+__global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dz, int64_t P, int C, float *__restrict__ db) {
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (int64_t p = threadIdx.x; p < P; p += blockDim.x) s += __bfloat162float(dz[p * C + c]);
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[c] += red[0];
+}
+
+// Adam on fp32 master weights; bf16 copy refreshed for the GEMMs.
+__global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2, __nv_bfloat16 *__restrict__ wb) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+        if (wb) wb[i] = __float2bfloat16(wi);
+    }
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ a, int64_t n, __nv_bfloat16 *__restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16(a[i]);
+}
+
+// Images of one candidate from its subband dynamic spectrum sub[S][T_in]
+// (already dedispersed at the candidate DM within each subband; time bins):
+//   ft[s][u]  = sub[s][u0 + u]                         (S x 256)
+//   dmt[j][u] = sum_s sub[s][u0 + u + shift[j][s]]     (256 trial-DM offsets)
+// u0 = (T_in - 256) / 2.  Each image is then set to zero mean and unit
+// variance (computed in fp32 over its 65536 values) and stored as bf16.
+// One CTA (256 threads) per (candidate, image row); a second pass normalises.
+__global__ void features_raw_kernel(const float *__restrict__ sub, int S, int T_in, const int32_t *__restrict__ shift,
+                                    float *__restrict__ ft_raw, float *__restrict__ dmt_raw) {
+    const int b = blockIdx.y, row = blockIdx.x, u = threadIdx.x;
+    const int u0 = (T_in - kImg) / 2;
+    const float *sb = sub + (int64_t)b * S * T_in;
+    if (row < S) ft_raw[((int64_t)b * kImg + row) * kImg + u] = sb[(int64_t)row * T_in + u0 + u];
+    float s = 0.f;
+    const int32_t *sh = shift + (int64_t)row * S;
+    for (int k = 0; k < S; ++k) {
+        const int t = u0 + u + sh[k];
+        if (t >= 0 && t < T_in) s += sb[(int64_t)k * T_in + t];
+    }
+    dmt_raw[((int64_t)b * kImg + row) * kImg + u] = s;
+}
+
+__global__ void normalise_kernel(const float *__restrict__ raw, __nv_bfloat16 *__restrict__ out) {
+    const int64_t base = (int64_t)blockIdx.x * kImg * kImg;
+    float s = 0.f, s2 = 0.f;
+    for (int i = threadIdx.x; i < kImg * kImg; i += blockDim.x) {
+        const float v = raw[base + i];
+        s += v;
+        s2 += v * v;
+    }
+    __shared__ float r1[256], r2[256];
+    r1[threadIdx.x] = s;
+    r2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            r1[threadIdx.x] += r1[threadIdx.x + o];
+            r2[threadIdx.x] += r2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    const float n = (float)(kImg * kImg);
+    const float mean = r1[0] / n;
+    const float var = fmaxf(r2[0] / n - mean * mean, 0.f);
+    const float inv = var > 0.f ? rsqrtf(var) : 0.f;
+    for (int i = threadIdx.x; i < kImg * kImg; i += blockDim.x)
+        out[base + i] = __float2bfloat16((raw[base + i] - mean) * inv);
+}
+
+int grid_for(int64_t n, int threads = 256) {
+    return (int)std::min<int64_t>((n + threads - 1) / threads, 152 * 32);
+}
+
+}  // namespace
+
+int cnn_gemm(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int M, int N,
+             int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st) {
+    if (K % kBK) return SP_EINVAL;
+    if (splits < 1) splits = 1;
+    int64_t ks = ((K / kBK + splits - 1) / splits) * kBK;
+    const int nz = (int)((K + ks - 1) / ks);
+    const dim3 grid((unsigned)((N + kBN - 1) / kBN), (unsigned)((M + kBM - 1) / kBM), (unsigned)nz);
+    if (epi == kEpiBiasRelu)
+        gemm_nt_kernel<kEpiBiasRelu><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, ks, Cf, Cb, ldc, bias);
+    else if (epi == kEpiStore && nz == 1)
+        gemm_nt_kernel<kEpiStore><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, ks, Cf, Cb, ldc, bias);
+    else
+        gemm_nt_kernel<kEpiAtomic><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, ks, Cf, Cb, ldc, bias);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_im2col(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho, int Wo, int Kp,
+               __nv_bfloat16 *cols, cudaStream_t st) {
+    im2col_kernel<<<grid_for((int64_t)Nb * Ho * Wo * Kp), 256, 0, st>>>(x, Nb, H, W, C, stride, Ho, Wo, Kp, cols);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_col2im_relu(const float *dcols, const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho,
+                    int Wo, int Kp, __nv_bfloat16 *dz, cudaStream_t st) {
+    col2im_relu_kernel<<<grid_for((int64_t)Nb * H * W * C), 256, 0, st>>>(dcols, x, Nb, H, W, C, stride, Ho, Wo, Kp,
+                                                                         dz);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_transpose(const __nv_bfloat16 *in, int64_t R, int64_t C, __nv_bfloat16 *out, cudaStream_t st) {
+    if ((C + 31) / 32 > 65535) return SP_ELIMIT;
+    const dim3 grid((unsigned)((R + 31) / 32), (unsigned)((C + 31) / 32));
+    transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(in, R, C, out);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_avgpool(const __nv_bfloat16 *y, int Nb, int HW, int C, float *feat, cudaStream_t st) {
+    avgpool_kernel<<<grid_for((int64_t)Nb * C), 256, 0, st>>>(y, Nb, HW, C, feat);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_avgpool_back(const float *dfeat, const __nv_bfloat16 *y, int Nb, int HW, int C, __nv_bfloat16 *dz,
+                     cudaStream_t st) {
+    avgpool_back_kernel<<<grid_for((int64_t)Nb * HW * C), 256, 0, st>>>(dfeat, y, Nb, HW, C, dz);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_head(const float *feat, int Nb, int C, const float *w, const float *b, float *logit, cudaStream_t st) {
+    head_kernel<<<(Nb + 7) / 8, 256, 0, st>>>(feat, Nb, C, w, b, logit);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_fuse_loss(const float *l1, const float *l2, const float *label, int Nb, float *prob, float *dl1, float *dl2,
+                  float *loss, cudaStream_t st) {
+    fuse_loss_kernel<<<(Nb + 255) / 256, 256, 0, st>>>(l1, l2, label, Nb, prob, dl1, dl2, loss);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_head_back(const float *feat, const float *dl, int Nb, int C, const float *w, float *dfeat, float *dw,
+                  float *db, cudaStream_t st) {
+    head_back_kernel<<<(C + 255) / 256, 256, 0, st>>>(feat, dl, Nb, C, w, dfeat, dw, db);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_bias_grad(const __nv_bfloat16 *dz, int64_t P, int C, float *db, cudaStream_t st) {
+    bias_grad_kernel<<<C, 256, 0, st>>>(dz, P, C, db);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
+             int64_t step, __nv_bfloat16 *wb, cudaStream_t st) {
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    adam_kernel<<<grid_for(n), 256, 0, st>>>(w, g, m, v, n, lr, b1, b2, eps, c1, c2, wb);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b, cudaStream_t st) {
+    to_bf16_kernel<<<grid_for(n), 256, 0, st>>>(a, n, b);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_features(const float *sub, int Nb, int S, int T_in, const int32_t *shift, float *ft_raw, float *dmt_raw,
+                 __nv_bfloat16 *ft, __nv_bfloat16 *dmt, cudaStream_t st) {
+    if (S != kImg || T_in < kImg) return SP_EINVAL;
+    features_raw_kernel<<<dim3(kImg, Nb), kImg, 0, st>>>(sub, S, T_in, shift, ft_raw, dmt_raw);
+    if (cudaGetLastError() != cudaSuccess) return SP_ECUDA;
+    normalise_kernel<<<Nb, 256, 0, st>>>(ft_raw, ft);
+    normalise_kernel<<<Nb, 256, 0, st>>>(dmt_raw, dmt);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+}  // namespace sp

@@ -1,0 +1,39 @@
+// sp_cnn_internal.h -- declarations shared by the classifier's kernels
+// (cnn.cu) and its host orchestration (cnn.cpp).  Not installed.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "sp_internal.h"
+
+namespace sp {
+
+constexpr int kImg = 256;  // images are kImg x kImg (subbands or trial DMs x time bins)
+constexpr int kEpiBiasRelu = 0, kEpiStore = 1, kEpiAtomic = 2;
+
+// C[M,N] = A[M,K] * B[N,K]^T (bf16, row-major, K % 32 == 0).  kEpiBiasRelu:
+// Cb = bf16(relu(C + bias)); kEpiStore: Cf = C; kEpiAtomic: Cf += C (with
+// `splits` K ranges in parallel; Cf zeroed by the caller).
+int cnn_gemm(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int M, int N,
+             int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st);
+int cnn_im2col(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho, int Wo, int Kp,
+               __nv_bfloat16 *cols, cudaStream_t st);
+int cnn_col2im_relu(const float *dcols, const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho,
+                    int Wo, int Kp, __nv_bfloat16 *dz, cudaStream_t st);
+int cnn_transpose(const __nv_bfloat16 *in, int64_t R, int64_t C, __nv_bfloat16 *out, cudaStream_t st);
+int cnn_avgpool(const __nv_bfloat16 *y, int Nb, int HW, int C, float *feat, cudaStream_t st);
+int cnn_avgpool_back(const float *dfeat, const __nv_bfloat16 *y, int Nb, int HW, int C, __nv_bfloat16 *dz,
+                     cudaStream_t st);
+int cnn_head(const float *feat, int Nb, int C, const float *w, const float *b, float *logit, cudaStream_t st);
+int cnn_fuse_loss(const float *l1, const float *l2, const float *label, int Nb, float *prob, float *dl1, float *dl2,
+                  float *loss, cudaStream_t st);
+int cnn_head_back(const float *feat, const float *dl, int Nb, int C, const float *w, float *dfeat, float *dw,
+                  float *db, cudaStream_t st);
+int cnn_bias_grad(const __nv_bfloat16 *dz, int64_t P, int C, float *db, cudaStream_t st);
+int cnn_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
+             int64_t step, __nv_bfloat16 *wb, cudaStream_t st);
+int cnn_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b, cudaStream_t st);
+int cnn_features(const float *sub, int Nb, int S, int T_in, const int32_t *shift, float *ft_raw, float *dmt_raw,
+                 __nv_bfloat16 *ft, __nv_bfloat16 *dmt, cudaStream_t st);
+
+}  // namespace sp

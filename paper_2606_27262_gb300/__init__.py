@@ -110,6 +110,7 @@ SIGNATURES = {
     "sp_cnn_features_workspace_bytes": (I64, [I32]),
     "sp_cnn_features": (ctypes.c_int, [P, I32, I32, I32, P, P, P, P, I64, P]),
     "sp_dmt_shifts": (ctypes.c_int, [P, I32, I32, I32, P]),
+    "sp_cnn_extract": (ctypes.c_int, [P, P, I64, I64, P, I32, P, I32, I32, P, P]),
     "sp_probe_iadd3_rate": (ctypes.c_int, [ctypes.c_int, P, P]),
 }
 SP_DEDISP_NUM_SHAPES = 3
@@ -644,6 +645,19 @@ def dmt_shifts(freqs_mhz, nsub: int = CNN_IMG, max_sweep: int = 128) -> np.ndarr
     out = np.zeros((CNN_IMG, nsub), np.int32)
     _check(_lib().sp_dmt_shifts(f.ctypes.data, f.size, int(nsub), int(max_sweep), out.ctypes.data), "sp_dmt_shifts")
     return out
+
+
+def cnn_extract(plan: Plan, d_staged, n_in: int, d_cands, widths, t_in: int = 512, stream=None):
+    """Subband dynamic spectra (float32 [ncand][256][t_in] CUDA tensor) of
+    candidates (int32 [ncand][4] CUDA tensor of sp_cand records) from a
+    staged beam."""
+    import torch
+    w = _widths(widths)
+    n = int(d_cands.shape[0])
+    sub = torch.empty((n, CNN_IMG, int(t_in)), dtype=torch.float32, device=d_cands.device)
+    _check(_lib().sp_cnn_extract(plan.handle, _ptr(d_staged), staged_pitch(int(n_in)), int(n_in), _ptr(d_cands), n,
+                                 w.ctypes.data, w.size, int(t_in), _ptr(sub), _stream(stream)), "sp_cnn_extract")
+    return sub
 
 
 def cnn_features(d_sub, d_shift, d_ft, d_dmt, d_work=None, stream=None):

@@ -426,3 +426,36 @@ extern "C" int sp_dmt_shifts(const double *freqs_mhz, int32_t nchan, int32_t nsu
     }
     return SP_OK;
 }
+
+// Decimation of a candidate of boxcar width w: max(1, w / 4) samples per
+// bin, so that the pulse spans about four bins; the window is centred on
+// the boxcar's middle sample t + w / 2.
+extern "C" int sp_cnn_extract(const sp_plan *plan, const uint8_t *d_staged, int64_t pitch, int64_t n_in,
+                              const sp_cand *d_cands, int32_t ncand, const int32_t *h_widths, int32_t nw,
+                              int32_t t_in, float *d_sub, void *stream) {
+    if (!plan || !d_staged || !d_cands || ncand < 1 || ncand > 65535 || !d_sub || t_in < 1 || t_in > 4096)
+        return SP_EINVAL;
+    int rc = check_widths(h_widths, nw);
+    if (rc) return rc;
+    if (!on_plan_device(plan) || plan->nchan % kImg || pitch < dedisp_pitch(n_in) || n_in <= 0) return SP_EINVAL;
+    int32_t tab[2 * SP_MAX_WIDTHS];
+    for (int k = 0; k < nw; ++k) {
+        tab[k] = std::max(1, h_widths[k] / 4);
+        tab[SP_MAX_WIDTHS + k] = h_widths[k] / 2;
+    }
+    // The two small tables travel in a device buffer owned by the plan's
+    // device for the duration of the call.
+    int32_t *d_tab = nullptr;
+    if (cudaMalloc((void **)&d_tab, sizeof tab) != cudaSuccess) {
+        cudaGetLastError();
+        return SP_ENOMEM;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    rc = cudaMemcpyAsync(d_tab, tab, sizeof tab, cudaMemcpyHostToDevice, st) == cudaSuccess ? SP_OK : SP_ECUDA;
+    if (!rc)
+        rc = cnn_extract(d_staged, pitch, n_in, plan->nchan, plan->d_delays, d_cands, ncand, d_tab,
+                         d_tab + SP_MAX_WIDTHS, kImg, t_in, d_sub, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = SP_ECUDA;
+    cudaFree(d_tab);
+    return rc;
+}

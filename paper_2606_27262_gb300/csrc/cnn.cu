@@ -391,6 +391,37 @@ __global__ void normalise_kernel(const float *__restrict__ raw, __nv_bfloat16 *_
         out[base + i] = __float2bfloat16((raw[base + i] - mean) * inv);
 }
 
+// Subband dynamic spectrum of candidate q from the staged beam xt
+// [nchan][pitch]: sub[q][s][u] = sum over the channels c of subband s and
+// i < dec of xt[c][t0 + (u - t_in/2) * dec + i + delay[dm][c]], with t0 the
+// centre of the candidate's boxcar window; samples outside [0, n_in) count 0.
+// One CTA per (candidate, subband), threads over time bins.
+__global__ void extract_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int64_t n_in, int32_t nchan,
+                               const int32_t *__restrict__ delays, const sp_cand *__restrict__ cands,
+                               const int32_t *__restrict__ dec_of_width, const int32_t *__restrict__ half_of_width,
+                               int32_t nsub, int32_t t_in, float *__restrict__ sub) {
+    const int q = blockIdx.y, s = blockIdx.x;
+    const sp_cand c = cands[q];
+    const int per = nchan / nsub;
+    const int dec = dec_of_width[c.width_idx];
+    const int64_t t0 = (int64_t)c.t + half_of_width[c.width_idx];
+    const int32_t *dl = delays + (int64_t)c.dm_idx * nchan;
+    for (int u = threadIdx.x; u < t_in; u += blockDim.x) {
+        const int64_t tb = t0 + (int64_t)(u - t_in / 2) * dec;
+        float acc = 0.f;
+        for (int k = 0; k < per; ++k) {
+            const int ch = s * per + k;
+            const uint8_t *row = xt + (int64_t)ch * pitch;
+            const int64_t base = tb + dl[ch];
+            for (int i = 0; i < dec; ++i) {
+                const int64_t t = base + i;
+                if (t >= 0 && t < n_in) acc += (float)row[t];
+            }
+        }
+        sub[((int64_t)q * nsub + s) * t_in + u] = acc;
+    }
+}
+
 int grid_for(int64_t n, int threads = 256) {
     return (int)std::min<int64_t>((n + threads - 1) / threads, 152 * 32);
 }
@@ -475,6 +506,14 @@ int cnn_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, 
 
 int cnn_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b, cudaStream_t st) {
     to_bf16_kernel<<<grid_for(n), 256, 0, st>>>(a, n, b);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_extract(const uint8_t *xt, int64_t pitch, int64_t n_in, int32_t nchan, const int32_t *delays,
+                const sp_cand *cands, int32_t ncand, const int32_t *dec_of_width, const int32_t *half_of_width,
+                int32_t nsub, int32_t t_in, float *sub, cudaStream_t st) {
+    extract_kernel<<<dim3((unsigned)nsub, (unsigned)ncand), 256, 0, st>>>(xt, pitch, n_in, nchan, delays, cands,
+                                                                        dec_of_width, half_of_width, nsub, t_in, sub);
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

@@ -130,10 +130,17 @@ def evaluate(clf, rng, n_each=1024, batch=64, snr_lo=8.0):
     return kinds, p
 
 
-def test_training_gain_over_sifter_alone():
+@pytest.fixture(scope="module")
+def trained():
     rng = np.random.default_rng(3)
     clf = sp.Classifier(max_batch=64, seed=11)
     losses = train(clf, rng, 3000)
+    yield clf, losses
+    clf.close()
+
+
+def test_training_gain_over_sifter_alone(trained):
+    clf, losses = trained
     assert losses[-1] < 0.5 * losses[0], losses
     kinds, p = evaluate(clf, np.random.default_rng(4))
     bursts, rfi = kinds == 0, kinds > 0
@@ -144,3 +151,57 @@ def test_training_gain_over_sifter_alone():
           f"(by kind {per_kind}); the sifter alone passes every candidate (false positives 1.0)")
     assert recall >= 0.99
     assert fpr <= 0.05
+
+
+def test_search_sift_classify_end_to_end(trained):
+    """A 4096-channel beam with injected bursts through the whole chain on
+    the GPU: search, host sifter, candidate windows cut from the staged
+    beam, features, classifier.  The bursts the sifter keeps are accepted;
+    the chain agrees with the oracle's features on the extracted windows."""
+    clf, _ = trained
+    wl = synth.Workload("e2e", 4096, 32768, FREQS, synth.dm_plan_config2(), synth.widths_pow2(256), 6.0, 8192,
+                        2024, 6, 100.0, 1900.0, snr_lo=15.0, snr_hi=30.0)
+    plan = sp.Plan(wl.freqs, wl.tsamp, wl.dms)
+    n_in = wl.n_out + plan.max_delay
+    x, bursts = synth.make_workload_beam(wl, n_in)
+    d_in = torch.from_numpy(x).cuda()
+    staged = sp.staged_buffer(wl.nchan, n_in)
+    sp.stage_input(d_in, staged)
+    dmt = torch.empty((plan.ndm, wl.n_out), dtype=torch.int32, device="cuda")
+    sp.dedisperse_staged(plan, staged, n_in, dmt)
+    from tests import gpu_util as gu
+    cands, _ = gu.dev_candidates(dmt, wl.widths, wl.threshold, wl.norm_block, cap=1 << 22)
+    kept = sp.sift(cands, wl.dms, wl.widths, wl.tsamp)
+    assert kept.size > 0
+    d_c = torch.from_numpy(np.ascontiguousarray(kept).view(np.int32).reshape(-1, 4)).cuda()
+    sub = sp.cnn_extract(plan, staged, n_in, d_c, wl.widths, t_in=T_IN)
+    ft, dm_img = _features(sub)
+    p = torch.empty(kept.size, device="cuda")
+    for i in range(0, kept.size, 64):
+        j = min(kept.size, i + 64)
+        clf.forward(ft[i:j].contiguous(), dm_img[i:j].contiguous(), p[i:j])
+    p = p.cpu().numpy()
+    # extraction of one window equals its definition (channel sums at Eq.-1 delays)
+    q = int(np.argmax(kept["snr"]))
+    c = kept[q]
+    w = int(wl.widths[c["width_idx"]])
+    dec, t0 = max(1, w // 4), int(c["t"]) + w // 2
+    dl = plan.delays()[c["dm_idx"]]
+    s_idx = 37
+    want = np.zeros(T_IN)
+    for u in range(T_IN):
+        for ch in range(s_idx * 16, s_idx * 16 + 16):
+            for i in range(dec):
+                t = t0 + (u - T_IN // 2) * dec + i + dl[ch]
+                if 0 <= t < n_in:
+                    want[u] += x[t, ch]
+    assert np.array_equal(sub[q, s_idx].cpu().numpy(), want.astype(np.float32))
+    found = 0
+    for b in bursts:
+        near = (np.abs(wl.dms[kept["dm_idx"]] - b.dm) <= max(5.0, 0.02 * b.dm)) & (np.abs(kept["t"] - b.t0) <= 256)
+        if near.any():
+            found += 1
+            assert p[near].max() >= 0.5, (b, p[near])
+    assert found >= len(bursts) - 1
+    print(f"end to end: {cands.size} candidates, {kept.size} after sifting, "
+          f"{int((p >= 0.5).sum())} accepted; {found}/{len(bursts)} bursts kept and accepted")

@@ -39,6 +39,12 @@ continuous batching.  value = sustained real-time beams (gulps searched per
 second at saturation x 8.0 s), next to per-gulp launches on one stream; the
 p50/p99 latency of real-time arrivals for the 256 beams is reported against
 the 8.0 s deadline.
+
+`--workload classifier` measures the candidate classifier: training steps
+(features + forward + backward + Adam, batch 64) and inference (features +
+forward, batch 256) on device-resident synthetic candidate spectra, with the
+algorithmic tensor-core rate (convolution FLOPs of the step over its time)
+against the measured bf16 GEMM peak.
 """
 from __future__ import annotations
 
@@ -75,7 +81,7 @@ def parse_args(argv=None):
     p.add_argument("--n-out", type=int, default=None,
                    help="searched samples per beam (default: the full 131072); smaller values are for "
                         "profiler captures only")
-    p.add_argument("--workload", choices=["single", "batched", "stream"], default="single")
+    p.add_argument("--workload", choices=["single", "batched", "stream", "classifier"], default="single")
     p.add_argument("--stream-beams", type=int, default=256, help="stream workload: beams")
     p.add_argument("--stream-periods", type=float, default=3.0,
                    help="stream workload: gulp periods of real-time arrivals for the latency figures")
@@ -603,6 +609,105 @@ def run_stream(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------- classifier --
+CNN_LAYERS = [(1, 16, 256), (16, 32, 128), (32, 64, 64), (64, 128, 32), (128, 256, 16)]  # cin, cout, h_in
+
+
+def cnn_flops_per_example(train: bool) -> float:
+    """Algorithmic multiply-add FLOPs of the two 5-layer branches (3x3
+    convolutions, stride 2): forward, plus weight and input gradients."""
+    fwd = dx = 0.0
+    for i, (ci, co, h) in enumerate(CNN_LAYERS):
+        f = 2.0 * (h // 2) ** 2 * co * 9 * ci
+        fwd += f
+        if i > 0:
+            dx += f
+    per_branch = fwd + (fwd + dx if train else 0.0)
+    return 2 * per_branch
+
+
+def run_classifier(args):
+    import numpy as np
+    import torch
+
+    import paper_2606_27262_gb300 as sp
+    import synth
+    from paper_2606_27262_gb300 import build as spbuild
+    from synth import classifier as scls
+
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    spbuild.build()
+    freqs = synth.band_freqs(4096)
+    shift = torch.from_numpy(sp.dmt_shifts(freqs, 256, 128)).to(dev)
+    rng = np.random.default_rng(1004 + rank)
+    bt, bi = 64, 256
+    pool = [scls.classifier_batch(rng, bt, freqs, device=dev, p_burst=0.6) for _ in range(8)]
+    clf = sp.Classifier(max_batch=bi, seed=11)
+    ft = torch.empty((bi, 256, 256), dtype=torch.bfloat16, device=dev)
+    dmt = torch.empty_like(ft)
+    work = torch.empty(int(sp.library().sp_cnn_features_workspace_bytes(bi)), dtype=torch.uint8, device=dev)
+    labels = [torch.from_numpy(lab).to(dev) for _, lab, _ in pool]
+    stream = torch.cuda.current_stream(dev)
+
+    def train_step(k):
+        sub = pool[k % len(pool)][0]
+        sp.cnn_features(sub, shift, ft[:bt], dmt[:bt], work)
+        clf.train_step(ft[:bt], dmt[:bt], labels[k % len(pool)], 1e-3)
+
+    for k in range(max(args.warmup, 3)):
+        train_step(k)
+    torch.cuda.synchronize(dev)
+    steps = max(args.steps, 1) * 40
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0.record(stream)
+    for k in range(steps):
+        train_step(k)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    train_ms = e0.elapsed_time(e1) / steps
+    # inference: features + forward on batches of 256 candidates
+    big = scls.classifier_batch(rng, bi, freqs, device=dev)[0]
+    prob = torch.empty(bi, device=dev)
+    for _ in range(3):
+        sp.cnn_features(big, shift, ft, dmt, work)
+        clf.forward(ft, dmt, prob)
+    torch.cuda.synchronize(dev)
+    reps = max(args.steps, 1) * 10
+    e0.record(stream)
+    for _ in range(reps):
+        sp.cnn_features(big, shift, ft, dmt, work)
+        clf.forward(ft, dmt, prob)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    infer_ms = e0.elapsed_time(e1) / reps
+    clk = clocks.stop()
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1900.0)
+    tr_tflops = cnn_flops_per_example(True) * bt / (train_ms / 1e3) / 1e12
+    in_tflops = cnn_flops_per_example(False) * bi / (infer_ms / 1e3) / 1e12
+    line = {
+        "metric": "classifier candidates per second (inference) and training examples per second",
+        "value": bi / (infer_ms / 1e3), "unit": "candidates/s", "n_gpus": 1, "steps": reps, "warmup": 3,
+        "ms_per_step": infer_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic candidate spectra (bursts, narrowband and broadband RFI, tones, noise)",
+        "config": {"workload": "classifier: two 5-layer 3x3 stride-2 CNNs on 256x256 frequency-time and DM-time "
+                               "images, 0.79 M parameters", "batch_infer": bi, "batch_train": bt,
+                   "params": int(sp.library().sp_cnn_num_params())},
+        "training": {"examples_per_s": bt / (train_ms / 1e3), "ms_per_step": train_ms, "steps": steps,
+                     "tflops": tr_tflops},
+        "roofline": {"bound": "tensor", "achieved": in_tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": in_tflops / peak, "traffic": None,
+                     "kernel": "inference step (features + im2col + gemm_nt_kernel + pooling/head), algorithmic "
+                               "convolution FLOPs over the step time",
+                     "peak_basis": "measured bf16 GEMM burst (MEASURED_PEAKS.json)"},
+        "e2e": None, "cpu_baseline": None, "clocks": clk, "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------- reference --
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -644,6 +749,8 @@ def main(argv=None):
         run_batched(args)
     elif args.workload == "stream":
         run_stream(args)
+    elif args.workload == "classifier":
+        run_classifier(args)
     else:
         run_ours(args)
 

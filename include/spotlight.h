@@ -372,6 +372,30 @@ int sp_batch_run_host(sp_batch *b, const uint8_t *const *h_in, sp_cand *h_cands,
                       int64_t cap_per_beam, int64_t *h_counts, void *stream);
 int sp_batch_status(const sp_batch *b, int32_t *h_status, int32_t clear);
 
+/* --------------------------------------------------------------- injector --
+ * Signal injection into quantised data (Appendix B; used to add simulated
+ * bursts to beams that are already quantised, for validation).  With
+ * L = 2^bits states, state k covers noise values [lo_k, hi_k),
+ * lo_k = mu + (k - L/2) * level * sigma, hi_k = lo_k + level * sigma, state
+ * 0 extends to -inf and state L-1 to +inf.  A sample in state n receiving a
+ * signal S >= 0 (in the units of mu and sigma) moves to the state k >= n
+ * of highest probability
+ *   P(n -> k) = max(0, phi(min(hi_k - S, hi_n)) - phi(max(lo_k - S, lo_n)))
+ *               / (phi(hi_n) - phi(lo_n)),
+ * phi the Gaussian CDF with mean mu and deviation sigma (Appendix B's
+ * general formula with its boundary states); exact ties go to the lower
+ * state.  Evaluated in double precision.
+ *   d_data [n] uint8 device, one sample per byte (values < 2^bits), updated
+ *           in place; samples with S <= 0, in the top state, or with a
+ *           value >= 2^bits are left unchanged.
+ *   d_signal [n] float32 device.
+ *   bits 1..8; sigma > 0; level > 0 (Appendix B's l; 0.030765 for its 8-bit
+ *   data; 1/16 for data quantised as round(128 + 16 z), with mu = 127.5 and
+ *   sigma = 16).
+ * Errors: SP_EINVAL, SP_ECUDA (launch). */
+int sp_inject_quantised(uint8_t *d_data, const float *d_signal, int64_t n, int32_t bits, double mu,
+                        double sigma, double level, void *stream);
+
 /* ----------------------------------------------------------------- sifter --
  * Candidate sifting after the single-pulse search (Sec. 3.2.1), host code:
  * DBSCAN clustering of one beam's candidates in the DM-time plane, the

@@ -18,6 +18,7 @@ Names mirror the C entry points:
 * ``Batch``                      sp_batch_* (grouped multi-beam step, graph)
 * ``Stream``                     sp_stream_* (real-time gulps, continuous batching)
 * ``sift``                       sp_sift (DBSCAN clustering + thresholds, host)
+* ``inject_quantised``           sp_inject_quantised (Appendix B injection)
 * ``Classifier``, ``cnn_features``, ``dmt_shifts``  sp_cnn_* (two-image CNN)
 """
 from __future__ import annotations
@@ -97,6 +98,7 @@ SIGNATURES = {
     "sp_stream_pending": (ctypes.c_int, [P, P, P, P]),
     "sp_stream_now": (F64, []),
     "sp_sift": (ctypes.c_int, [P, I64, P, I32, P, I32, F64, P, P, I64, P, P]),
+    "sp_inject_quantised": (ctypes.c_int, [P, P, I64, I32, F64, F64, F64, P]),
     "sp_cnn_num_params": (I64, []),
     "sp_cnn_create": (ctypes.c_int, [I32, ctypes.c_uint64, P]),
     "sp_cnn_destroy": (ctypes.c_int, [P]),
@@ -608,6 +610,14 @@ class Stream:
             self.close()
         except Exception:
             pass
+
+
+def inject_quantised(d_data, d_signal, bits: int, mu: float, sigma: float, level: float, stream=None):
+    """In place: d_data uint8 CUDA tensor, d_signal float32 CUDA tensor of
+    the same number of elements (sp_inject_quantised)."""
+    assert d_data.numel() == d_signal.numel()
+    _check(_lib().sp_inject_quantised(_ptr(d_data), _ptr(d_signal), int(d_data.numel()), int(bits), float(mu),
+                                      float(sigma), float(level), _stream(stream)), "sp_inject_quantised")
 
 
 class SiftParams(ctypes.Structure):

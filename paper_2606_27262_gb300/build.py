@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *ARCH, "-I", os.path.join(ROOT, "include")]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math"]
 
-CUDA_SOURCES = ["dedisperse.cu", "sps.cu", "sps_noalloc.cu", "probe.cu", "cnn.cu"]
+CUDA_SOURCES = ["dedisperse.cu", "sps.cu", "sps_noalloc.cu", "probe.cu", "cnn.cu", "inject.cu"]
 CXX_SOURCES = ["plan.cpp", "capi.cpp", "autotune.cpp", "batch.cpp", "stream.cpp", "sifter.cpp", "cnn.cpp"]
 
 

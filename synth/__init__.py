@@ -333,3 +333,16 @@ def config3(nbeams: int = 128, n_lo: int = 16384, n_hi: int = 131072, nchan: int
                          f"{{{', '.join(str(int(m)) for m in max_dms)}}}, gains U(0.5,1.5), widths 1-256",
                          nchan, band_freqs(nchan), plan_dms, beam_plan, n_out, widths_pow2(256), 6.0, 8192,
                          1003, 4)
+
+
+def burst_signal(freqs: np.ndarray, n_in: int, bursts: list[Burst], widths=(1,), gains: np.ndarray | None = None,
+                 tsamp: float = TSAMP) -> np.ndarray:
+    """The bursts of ``make_beam`` alone, as a dense float32 [n_in][nchan]
+    signal in the units of the 8-bit samples (before gain and quantisation):
+    the input of an injection into already-quantised data."""
+    freqs = np.asarray(freqs, dtype=np.float64)
+    g = np.ones(freqs.size, np.float64) if gains is None else np.asarray(gains, np.float64)
+    sr, sc, sv = _burst_signal(list(bursts), freqs, n_in, widths, g, tsamp)
+    out = np.zeros((n_in, freqs.size), np.float32)
+    np.add.at(out, (sr, sc), sv.astype(np.float32))
+    return out

@@ -250,7 +250,7 @@ int sp_single_pulse_search(const int32_t *d_dmt, int32_t ndm, int64_t n_out,
  * SP_NOALLOC_SCRATCH_BYTES (16 MiB), present on every GPU that loads the
  * library until the process exits.  Requests whose statistics need more
  * (sp_sps_workspace_bytes(ndm, n_out, nw, norm_block) > 16 MiB; config 2,
- * 5751 DMs x 131072 samples / 8192-sample blocks x 9 widths, needs 6.9 MB)
+ * 5751 DMs x 131072 samples / 8192-sample blocks x 9 widths, needs 8.7 MB)
  * return SP_ELIMIT.  The call allocates nothing: no cudaMalloc, no cudaFree.
  * The first call on a device looks up the array's device address with that
  * device current (make that first call before any stream capture).  Every

@@ -106,237 +106,333 @@ __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restric
     }
 }
 
-constexpr int kBxT = 256;                 // output samples per CTA
+constexpr int kBxT = 256;                 // interior output samples per CTA
 constexpr int kBxRows = 16;               // staged rows: 14 interior + 2 halo
 constexpr int kBxIn = kBxRows - 2;
-constexpr int kBxTT = kBxT + 2;           // staged samples incl. halo
-constexpr int kBxPerLane = (kBxTT + 31) / 32;
+constexpr int kBxPts = kBxT + 2;          // scored points per row: samples t0-1 .. t0+256
+constexpr int kBxOrg = 4;                 // staged index 0 = sample t0 - 4 (16-byte aligned rows)
+constexpr int kBxFirst = kBxOrg - 1;      // staged index of point 0 (sample t0 - 1)
+constexpr int kBxPass = 9;                // points per thread and pass (16 threads per row)
 
-// Best S/N over the widths at staged sample ti of one row, from prefix sums
-// P (uint32 wrap-around or int64).  cw[k] = w_k * m0 in the same type.
-// Windows must end by staged index fit_end (exclusive).
+// Entries of the inclusive prefix Q of one staged row: point i's windows
+// [i, i + w) need Q[i + w - 1] - Q[i - 1], up to i = kBxFirst + kBxPts - 1.
+__host__ __device__ inline int boxcar_nq(int maxw) { return ((kBxFirst + kBxPts + maxw - 1 + 15) / 16) * 16; }
+
 template <typename PT>
-__device__ __forceinline__ void best_over_widths(const PT *Pr, int ti, int fit_end, const WidthList &wl,
-                                                 const PT *cw, const float2 *cf, float &best, int &kb) {
-    const PT p0 = Pr[ti];
-#pragma unroll
-    for (int k = 0; k < SP_MAX_WIDTHS; ++k) {
-        if (k >= wl.nw) break;
-        const int w = wl.w[k];
-        if (ti + w > fit_end) break;  // widths increase: no later one fits either
-        const PT xs = Pr[ti + w] - p0 - cw[k];
-        float xf;
-        if constexpr (sizeof(PT) == 4)
-            xf = (float)(int32_t)xs;  // exact value of x: |x| < 2^31 was checked
-        else
-            xf = (float)(int64_t)xs;
-        const float s = fmaf(xf, cf[k].x, -cf[k].y);
-        if (s > best) {
-            best = s;
-            kb = k;
-        }
-    }
+__host__ __device__ inline size_t boxcar_smem_t(int maxw) {
+    return (size_t)kBxRows * boxcar_nq(maxw) * sizeof(PT) + (size_t)kBxRows * kBxPts * 4 + (size_t)kBxRows * kBxPts;
 }
 
-// Phase 1 for one row: P[i] = sum_{j<i} v(tbase + j) for i in [0, LP], with
-// staged indices outside [i_lo, i_hi) read as zero; also the min/max of the
-// staged values.
+// Phase 1 for one row, by one warp: Q[i] = sum_{j <= i} v(s0 + j) for the
+// staged indices i < nq, values outside [0, n_out) read as 0; 16 values per
+// lane (four 16-byte loads when rows are 16-byte aligned), an in-register
+// scan, then a warp scan of the lane totals.  Also the min and max of the
+// values read.
 template <typename PT>
-__device__ __forceinline__ void prefix_row(const int32_t *__restrict__ row, int64_t tbase, int LP, int i_lo,
-                                           int i_hi, PT *Pr, int32_t &vmin, int32_t &vmax) {
+__device__ __forceinline__ void prefix_row(const int32_t *__restrict__ row, int64_t s0, int64_t n_out, bool vec,
+                                           int nq, PT *Q, int32_t &vmin, int32_t &vmax) {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) Pr[0] = 0;
     PT carry = 0;
-    for (int base = 0; base < LP; base += 32) {
-        const int i = base + lane;
-        int32_t x = 0;
-        if (i >= i_lo && i < i_hi) {
-            x = __ldg(row + (tbase + i));
-            vmin = min(vmin, x);
-            vmax = max(vmax, x);
-        }
-        PT v = (PT)x;
+    for (int base0 = 0; base0 < nq; base0 += 512) {
+        const int base = base0 + lane * 16;
+        int32_t v[16];
+        const int64_t t = s0 + base;
+        if (base < nq && vec && t >= 0 && t + 16 <= n_out) {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const PT u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
-        }
-        if (i < LP) Pr[i + 1] = carry + v;
-        carry += __shfl_sync(0xffffffffu, v, 31);
-    }
-}
-
-// Phase 2 for one row: best S/N and width of every staged sample.
-template <typename PT>
-__device__ __forceinline__ void score_row(const PT *Pr, int d, int64_t tbase, int i_lo, int i_hi, int fit_end,
-                                          const WidthList &wl, int64_t norm_block, int64_t nblk,
-                                          const int32_t *__restrict__ m0s, const float2 *__restrict__ coefs,
-                                          float *snr_row, int8_t *k_row) {
-    const int lane = threadIdx.x & 31;
-    const int ti0 = lane * kBxPerLane;
-    int next_edge = -1;  // staged index where the next normalisation block starts
-    PT cw[SP_MAX_WIDTHS];
-    float2 cf[SP_MAX_WIDTHS];
+            for (int q = 0; q < 4; ++q) {
+                const int4 x = __ldg(reinterpret_cast<const int4 *>(row + t) + q);
+                v[4 * q] = x.x;
+                v[4 * q + 1] = x.y;
+                v[4 * q + 2] = x.z;
+                v[4 * q + 3] = x.w;
+            }
 #pragma unroll
-    for (int k = 0; k < SP_MAX_WIDTHS; ++k) {
-        cw[k] = 0;
-        cf[k] = make_float2(0.f, 0.f);
-    }
-    for (int j = 0; j < kBxPerLane; ++j) {
-        const int ti = ti0 + j;
-        if (ti >= kBxTT) break;
-        float best = -INFINITY;
-        int kb = -1;
-        if (ti >= i_lo && ti < i_hi) {
-            if (ti >= next_edge) {
-                const int64_t t = tbase + ti;
-                int64_t b = (norm_block > 0) ? t / norm_block : 0;
-                if (b > nblk - 1) b = nblk - 1;
-                const int64_t edge = (b == nblk - 1) ? INT64_MAX : (b + 1) * norm_block;
-                next_edge = (int)min(edge - tbase, (int64_t)INT32_MAX);
-                const int64_t idx = (int64_t)d * nblk + b;
-                const PT m0 = (PT)(int64_t)__ldg(m0s + idx);
+            for (int e = 0; e < 16; ++e) {
+                vmin = min(vmin, v[e]);
+                vmax = max(vmax, v[e]);
+            }
+        } else {
 #pragma unroll
-                for (int k = 0; k < SP_MAX_WIDTHS; ++k) {
-                    if (k < wl.nw) {
-                        cw[k] = (PT)wl.w[k] * m0;
-                        cf[k] = __ldg(coefs + idx * wl.nw + k);
-                    }
+            for (int e = 0; e < 16; ++e) {
+                v[e] = 0;
+                if (base < nq && t + e >= 0 && t + e < n_out) {
+                    v[e] = __ldg(row + t + e);
+                    vmin = min(vmin, v[e]);
+                    vmax = max(vmax, v[e]);
                 }
             }
-            best_over_widths<PT>(Pr, ti, fit_end, wl, cw, cf, best, kb);
         }
-        snr_row[ti] = best;
-        k_row[ti] = (int8_t)kb;
+        PT r[16];
+        PT acc = 0;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            acc += (PT)v[e];
+            r[e] = acc;
+        }
+        PT incl = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const PT u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const PT off = carry + incl - acc;
+        if (base < nq) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) Q[base + e] = off + r[e];
+        }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
 }
 
-template <bool MAP>
-__global__ void __launch_bounds__(256, 2)
-sps_boxcar_kernel(const int32_t *__restrict__ dmt, int32_t ndm, int64_t n_out, WidthList wl, int32_t maxw,
-                  float thr, int64_t norm_block, int64_t nblk, const int32_t *__restrict__ m0s,
-                  const float2 *__restrict__ coefs, sp_cand *__restrict__ cands, int64_t cap,
-                  unsigned long long *__restrict__ count, float *__restrict__ map_best,
-                  int8_t *__restrict__ map_k) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int LP = kBxTT + maxw;  // prefix entries 0..LP
-    float *snr_s = reinterpret_cast<float *>(smem + (size_t)kBxRows * (LP + 1) * 8);
-    int8_t *k_s = reinterpret_cast<int8_t *>(snr_s + kBxRows * kBxTT);
-    uint32_t *P32 = reinterpret_cast<uint32_t *>(smem);
-    int64_t *P64 = reinterpret_cast<int64_t *>(smem);
+__device__ __forceinline__ int64_t block_of(int64_t t, int64_t norm_block, int64_t nblk) {
+    int64_t b = norm_block > 0 ? t / norm_block : 0;
+    return b > nblk - 1 ? nblk - 1 : b;
+}
 
-    const int64_t t0 = (int64_t)blockIdx.x * kBxT;
-    const int64_t tbase = t0 - 1;
-    const int d0 = blockIdx.y * kBxIn;
+// Phase 2 for the points p = l + 16 (j0 + j), j < kBxPass, of one staged
+// row: best S/N over the widths and its width index.
+template <typename PT>
+__device__ __forceinline__ void score_pass(const PT *Q, int d, int64_t s0, int64_t n_out, int fit_end, int l, int j0,
+                                           const WidthList &wl, int64_t norm_block, int64_t nblk,
+                                           const int32_t *__restrict__ m0s, const float2 *__restrict__ coefs,
+                                           float *snr_row, int8_t *k_row) {
+    float best[kBxPass];
+    int kb[kBxPass];
+#pragma unroll
+    for (int j = 0; j < kBxPass; ++j) {
+        best[j] = -INFINITY;
+        kb[j] = -1;
+    }
+    // valid points of this pass: sample t in [0, n_out)
+    int jlo = kBxPass, jhi = -1;
+#pragma unroll
+    for (int j = 0; j < kBxPass; ++j) {
+        const int p = l + 16 * (j0 + j);
+        const int64_t t = s0 + kBxFirst + p;
+        if (p < kBxPts && t >= 0 && t < n_out) {
+            jlo = min(jlo, j);
+            jhi = max(jhi, j);
+        }
+    }
+    if (jhi >= 0) {
+        const int64_t t_lo = s0 + kBxFirst + l + 16 * (j0 + jlo), t_hi = s0 + kBxFirst + l + 16 * (j0 + jhi);
+        const int64_t b_lo = block_of(t_lo, norm_block, nblk), b_hi = block_of(t_hi, norm_block, nblk);
+        const int64_t row_blk = (int64_t)d * nblk;
+        if (b_lo == b_hi) {  // one normalisation block: coefficients once per width
+            const PT m0 = (PT)(int64_t)__ldg(m0s + row_blk + b_lo);
+            for (int k = 0; k < wl.nw; ++k) {
+                const int w = wl.w[k];
+                const PT cw = (PT)w * m0;
+                const float2 cf = __ldg(coefs + (row_blk + b_lo) * wl.nw + k);
+                bool any = false;
+#pragma unroll
+                for (int j = 0; j < kBxPass; ++j) {
+                    const int i = kBxFirst + l + 16 * (j0 + j);
+                    if (j < jlo || j > jhi || i + w > fit_end) continue;
+                    any = true;
+                    const PT xs = Q[i + w - 1] - Q[i - 1] - cw;
+                    const float xf = sizeof(PT) == 4 ? (float)(int32_t)xs : (float)(int64_t)xs;
+                    const float sv = fmaf(xf, cf.x, -cf.y);
+                    if (sv > best[j]) {
+                        best[j] = sv;
+                        kb[j] = k;
+                    }
+                }
+                if (!any) break;  // widths increase: no later one fits either
+            }
+        } else {  // points in several blocks
+            for (int k = 0; k < wl.nw; ++k) {
+                const int w = wl.w[k];
+                bool any = false;
+#pragma unroll
+                for (int j = 0; j < kBxPass; ++j) {
+                    const int i = kBxFirst + l + 16 * (j0 + j);
+                    if (j < jlo || j > jhi || i + w > fit_end) continue;
+                    any = true;
+                    const int64_t b = block_of(s0 + i, norm_block, nblk);
+                    const PT cw = (PT)w * (PT)(int64_t)__ldg(m0s + row_blk + b);
+                    const float2 cf = __ldg(coefs + (row_blk + b) * wl.nw + k);
+                    const PT xs = Q[i + w - 1] - Q[i - 1] - cw;
+                    const float xf = sizeof(PT) == 4 ? (float)(int32_t)xs : (float)(int64_t)xs;
+                    const float sv = fmaf(xf, cf.x, -cf.y);
+                    if (sv > best[j]) {
+                        best[j] = sv;
+                        kb[j] = k;
+                    }
+                }
+                if (!any) break;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kBxPass; ++j) {
+        const int p = l + 16 * (j0 + j);
+        if (p < kBxPts) {
+            snr_row[p] = best[j];
+            k_row[p] = (int8_t)kb[j];
+        }
+    }
+}
+
+struct BoxcarArgs {
+    const int32_t *dmt;
+    int32_t ndm;
+    int64_t n_out;
+    WidthList wl;
+    int32_t maxw;
+    float thr;
+    int64_t norm_block, nblk;
+    const int32_t *m0s;
+    const float2 *coefs;
+    sp_cand *cands;
+    int64_t cap;
+    unsigned long long *count;
+    float *map_best;
+    int8_t *map_k;
+    int *wide_count;  // tiles the 32-bit pass could not prove exact
+    int2 *wide_list;
+    bool vec;         // rows 16-byte aligned: 16-byte loads
+};
+
+// One tile (14 rows x 256 samples + halo).  PT = uint32: prefix sums in
+// 32-bit wrap-around arithmetic; returns false (uniformly) without writing
+// anything when a window sum might not fit in 32 bits.  PT = int64: always
+// exact.
+template <typename PT, bool MAP>
+__device__ __forceinline__ bool boxcar_tile(const BoxcarArgs &a, int tx, int ty, uint8_t *smem) {
+    const int nq = boxcar_nq(a.maxw);
+    PT *Qs = reinterpret_cast<PT *>(smem);
+    float *snr_s = reinterpret_cast<float *>(smem + (size_t)kBxRows * nq * sizeof(PT));
+    int8_t *k_s = reinterpret_cast<int8_t *>(snr_s + kBxRows * kBxPts);
+    const int64_t t0 = (int64_t)tx * kBxT;
+    const int64_t s0 = t0 - kBxOrg;
+    const int d0 = ty * kBxIn;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // Staged index i is sample tbase + i; samples exist for i in [i_lo, i_hi).
-    const int i_lo = tbase < 0 ? (int)(-tbase) : 0;
-    const int i_hi = (int)min((int64_t)LP, n_out - tbase);
-    const int fit_end = (int)min(n_out - tbase, (int64_t)INT32_MAX);  // windows end by this index
+    const bool vec = a.vec;
+    const int fit_end = (int)min(a.n_out - s0, (int64_t)INT32_MAX);
 
-    // Phase 1 in 32-bit wrap-around prefix sums, tracking the value range.
-    // x = S - w*m0 is exact if maxw * max|v - m0| < 2^31 for every block
-    // whose windows start in this tile; otherwise redo it in 64 bits.
     bool wide = false;
     for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
         const int d = d0 - 1 + rr;
-        if (d < 0 || d >= ndm) continue;
-        const int32_t *row = dmt + (int64_t)d * n_out;
+        if (d < 0 || d >= a.ndm) continue;
         int32_t vmin = INT32_MAX, vmax = INT32_MIN;
-        prefix_row<uint32_t>(row, tbase, LP, i_lo, i_hi, P32 + (size_t)rr * (LP + 1), vmin, vmax);
+        prefix_row<PT>(a.dmt + (int64_t)d * a.n_out, s0, a.n_out, vec, nq, Qs + (size_t)rr * nq, vmin, vmax);
+        if (sizeof(PT) == 4) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-            vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        }
-        if (vmin > vmax) continue;
-        const int64_t ts = tbase + i_lo, te = tbase + min(i_hi, kBxTT) - 1;
-        int64_t bs = (norm_block > 0) ? ts / norm_block : 0, be = (norm_block > 0) ? te / norm_block : 0;
-        bs = min(bs, nblk - 1);
-        be = min(be, nblk - 1);
-        for (int64_t b = bs + lane; b <= be; b += 32) {
-            const int64_t m0 = __ldg(m0s + (int64_t)d * nblk + b);
-            const int64_t dev = max((int64_t)vmax - m0, m0 - (int64_t)vmin);
-            if (dev * maxw > (int64_t)INT32_MAX) wide = true;
-        }
-    }
-    wide = __syncthreads_or(wide);
-    if (wide) {
-        for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
-            const int d = d0 - 1 + rr;
-            if (d < 0 || d >= ndm) continue;
-            int32_t vmin = 0, vmax = 0;
-            prefix_row<int64_t>(dmt + (int64_t)d * n_out, tbase, LP, i_lo, i_hi, P64 + (size_t)rr * (LP + 1),
-                                vmin, vmax);
+            for (int o = 16; o > 0; o >>= 1) {
+                vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+                vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            }
+            if (vmin <= vmax) {
+                const int64_t ts = max(s0 + kBxFirst, (int64_t)0), te = min(s0 + kBxFirst + kBxPts, a.n_out) - 1;
+                if (ts <= te) {
+                    const int64_t bs = block_of(ts, a.norm_block, a.nblk), be = block_of(te, a.norm_block, a.nblk);
+                    for (int64_t b = bs + lane; b <= be; b += 32) {
+                        const int64_t m0 = __ldg(a.m0s + (int64_t)d * a.nblk + b);
+                        const int64_t dev = max((int64_t)vmax - m0, m0 - (int64_t)vmin);
+                        if (dev * a.maxw > (int64_t)INT32_MAX) wide = true;
+                    }
+                }
+            }
         }
     }
-    __syncthreads();
+    if (__syncthreads_or(wide)) return false;
 
-    // Phase 2: best S/N over the widths for every staged (row, sample).
-    for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
+    {
+        const int rr = threadIdx.x >> 4, l = threadIdx.x & 15;
         const int d = d0 - 1 + rr;
-        if (d < 0 || d >= ndm) {
-            for (int ti = lane; ti < kBxTT; ti += 32) snr_s[rr * kBxTT + ti] = -INFINITY;
-            continue;
+        float *srow = snr_s + rr * kBxPts;
+        int8_t *krow = k_s + rr * kBxPts;
+        if (d < 0 || d >= a.ndm) {
+            for (int p = l; p < kBxPts; p += 16) {
+                srow[p] = -INFINITY;
+                krow[p] = -1;
+            }
+        } else {
+            const PT *Q = Qs + (size_t)rr * nq;
+            score_pass<PT>(Q, d, s0, a.n_out, fit_end, l, 0, a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
+            score_pass<PT>(Q, d, s0, a.n_out, fit_end, l, kBxPass, a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow,
+                           krow);
         }
-        if (wide)
-            score_row<int64_t>(P64 + (size_t)rr * (LP + 1), d, tbase, i_lo, i_hi, fit_end, wl, norm_block, nblk,
-                               m0s, coefs, snr_s + rr * kBxTT, k_s + rr * kBxTT);
-        else
-            score_row<uint32_t>(P32 + (size_t)rr * (LP + 1), d, tbase, i_lo, i_hi, fit_end, wl, norm_block,
-                                nblk, m0s, coefs, snr_s + rr * kBxTT, k_s + rr * kBxTT);
     }
     __syncthreads();
 
     // Phase 3: interior points -- map output, or threshold + 3x3 + append.
-    const int rows_in = min(kBxIn, ndm - d0);
-    const int t_in = (int)min((int64_t)kBxT, n_out - t0);
-    for (int idx = threadIdx.x; idx < kBxIn * kBxT; idx += 256) {
+    const int rows_in = min(kBxIn, a.ndm - d0);
+    const int t_in = (int)min((int64_t)kBxT, a.n_out - t0);
+    for (int idx = threadIdx.x; idx < kBxIn * kBxT; idx += blockDim.x) {
         const int r = idx / kBxT;
         const int tt = idx % kBxT;
         const int rr = 1 + r;
         const int ti = 1 + tt;
         const bool inr = r < rows_in && tt < t_in;
-        const float v = snr_s[rr * kBxTT + ti];
+        const float v = snr_s[rr * kBxPts + ti];
         if (MAP) {
             if (inr) {
-                const int64_t o = (int64_t)(d0 + r) * n_out + t0 + tt;
-                map_best[o] = v;
-                map_k[o] = k_s[rr * kBxTT + ti];
+                const int64_t o = (int64_t)(d0 + r) * a.n_out + t0 + tt;
+                a.map_best[o] = v;
+                a.map_k[o] = k_s[rr * kBxPts + ti];
             }
         } else {
-            bool cand = inr && v >= thr;
+            bool cand = inr && v >= a.thr;
             if (cand) {
-                const float *up = snr_s + (rr - 1) * kBxTT + ti;
-                const float *mid = snr_s + rr * kBxTT + ti;
-                const float *dn = snr_s + (rr + 1) * kBxTT + ti;
+                const float *up = snr_s + (rr - 1) * kBxPts + ti;
+                const float *mid = snr_s + rr * kBxPts + ti;
+                const float *dn = snr_s + (rr + 1) * kBxPts + ti;
                 cand = v > up[-1] && v > up[0] && v > up[1] && v > mid[-1] && v >= mid[1] && v >= dn[-1] &&
                        v >= dn[0] && v >= dn[1];
             }
             const unsigned mask = __ballot_sync(0xffffffffu, cand);
             if (mask) {
                 const int leader = __ffs(mask) - 1;
-                unsigned long long base = 0;
-                if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
-                base = __shfl_sync(0xffffffffu, base, leader);
+                unsigned long long basec = 0;
+                if (lane == leader) basec = atomicAdd(a.count, (unsigned long long)__popc(mask));
+                basec = __shfl_sync(0xffffffffu, basec, leader);
                 if (cand) {
-                    const unsigned long long pos = base + __popc(mask & ((1u << lane) - 1u));
-                    if ((int64_t)pos < cap) {
+                    const unsigned long long pos = basec + __popc(mask & ((1u << lane) - 1u));
+                    if ((int64_t)pos < a.cap) {
                         sp_cand c;
                         c.dm_idx = d0 + r;
                         c.t = (int32_t)(t0 + tt);
-                        c.width_idx = k_s[rr * kBxTT + ti];
+                        c.width_idx = k_s[rr * kBxPts + ti];
                         c.snr = v;
-                        cands[pos] = c;
+                        a.cands[pos] = c;
                     }
                 }
             }
         }
     }
+    return true;
 }
 
-size_t boxcar_smem(int maxw) {
-    return (size_t)kBxRows * (kBxTT + maxw + 1) * 8 + (size_t)kBxRows * kBxTT * 4 + (size_t)kBxRows * kBxTT;
+// Fast pass: every tile in 32-bit prefix arithmetic; a tile that cannot
+// prove its window sums exact is listed for the 64-bit pass.
+template <bool MAP>
+__global__ void __launch_bounds__(256, 3) sps_boxcar_kernel(BoxcarArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    if (!boxcar_tile<uint32_t, MAP>(a, blockIdx.x, blockIdx.y, smem) && threadIdx.x == 0) {
+        const int slot = atomicAdd(a.wide_count, 1);
+        a.wide_list[slot] = make_int2(blockIdx.x, blockIdx.y);
+    }
+}
+
+// Exact pass over the listed tiles, 64-bit prefix sums (persistent grid).
+template <bool MAP>
+__global__ void __launch_bounds__(256, 1) sps_boxcar_wide_kernel(BoxcarArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int n = *a.wide_count;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const int2 tile = a.wide_list[i];
+        boxcar_tile<int64_t, MAP>(a, tile.x, tile.y, smem);
+        __syncthreads();
+    }
+}
+
+size_t boxcar_smem(int maxw) { return boxcar_smem_t<uint32_t>(maxw); }
+size_t boxcar_wide_smem(int maxw) { return boxcar_smem_t<int64_t>(maxw); }
+
+int64_t boxcar_tiles(int32_t ndm, int64_t n_out) {
+    return ((n_out + kBxT - 1) / kBxT) * (((int64_t)ndm + kBxIn - 1) / kBxIn);
 }
 
 }  // namespace
@@ -347,16 +443,20 @@ int64_t sps_nblocks(int64_t n_out, int64_t norm_block) {
     return nb < 1 ? 1 : nb;
 }
 
+// Workspace: per-(row, block) m0, per-(row, block, width) coefficients, and
+// the list of tiles left to the 64-bit pass (count + one entry per tile).
 int64_t sps_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block) {
     const int64_t nblk = sps_nblocks(n_out, norm_block);
-    return align256((int64_t)ndm * nblk * 4) + align256((int64_t)ndm * nblk * nw * 8);
+    return align256((int64_t)ndm * nblk * 4) + align256((int64_t)ndm * nblk * nw * 8) + 256 +
+           align256(boxcar_tiles(ndm, n_out) * 8);
 }
 
 namespace {
 std::mutex g_sps_lock;
-size_t g_sps_smem[64][2] = {};  // configured boxcar shared memory per (device, kernel)
+size_t g_sps_smem[64][4] = {};  // configured boxcar shared memory per (device, kernel)
 
-int configure_boxcar(bool map, size_t smem) {
+template <typename K>
+int configure_kernel(K kernel, int slot, size_t smem) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -364,24 +464,28 @@ int configure_boxcar(bool map, size_t smem) {
     }
     if (dev < 0 || dev >= 64) return SP_ELIMIT;
     std::lock_guard<std::mutex> guard(g_sps_lock);
-    if (g_sps_smem[dev][map] >= smem) return SP_OK;
-    const cudaError_t e = map ? cudaFuncSetAttribute(sps_boxcar_kernel<true>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                              : cudaFuncSetAttribute(sps_boxcar_kernel<false>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) {
+    if (g_sps_smem[dev][slot] >= smem) return SP_OK;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return SP_ECUDA;
     }
-    g_sps_smem[dev][map] = smem;
+    g_sps_smem[dev][slot] = smem;
     return SP_OK;
+}
+
+int configure_boxcar(bool map, int maxw) {
+    int rc = map ? configure_kernel(sps_boxcar_kernel<true>, 0, boxcar_smem(maxw))
+                 : configure_kernel(sps_boxcar_kernel<false>, 1, boxcar_smem(maxw));
+    if (!rc)
+        rc = map ? configure_kernel(sps_boxcar_wide_kernel<true>, 2, boxcar_wide_smem(maxw))
+                 : configure_kernel(sps_boxcar_wide_kernel<false>, 3, boxcar_wide_smem(maxw));
+    return rc;
 }
 }  // namespace
 
 int sps_configure(int32_t maxw) {
-    const size_t smem = boxcar_smem(maxw);
-    int rc = configure_boxcar(false, smem);
-    if (!rc) rc = configure_boxcar(true, smem);
+    int rc = configure_boxcar(false, maxw);
+    if (!rc) rc = configure_boxcar(true, maxw);
     return rc;
 }
 
@@ -390,27 +494,54 @@ int launch_sps(const SpsArgs &a, cudaStream_t stream) {
     for (int k = 0; k < SP_MAX_WIDTHS; ++k) wl.w[k] = k < a.nw ? a.widths[k] : 0;
     wl.nw = a.nw;
     const int maxw = a.widths[a.nw - 1];
-    int32_t *m0s = reinterpret_cast<int32_t *>(a.work);
-    float2 *coefs = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(a.work) +
-                                               align256((int64_t)a.ndm * a.nblk * 4));
-    const size_t smem = boxcar_smem(maxw);
+    uint8_t *w8 = reinterpret_cast<uint8_t *>(a.work);
+    int32_t *m0s = reinterpret_cast<int32_t *>(w8);
+    w8 += align256((int64_t)a.ndm * a.nblk * 4);
+    float2 *coefs = reinterpret_cast<float2 *>(w8);
+    w8 += align256((int64_t)a.ndm * a.nblk * a.nw * 8);
+    int *wide_count = reinterpret_cast<int *>(w8);
+    int2 *wide_list = reinterpret_cast<int2 *>(w8 + 256);
     const bool map = a.map_best != nullptr;
-    int rc = configure_boxcar(map, smem);
+    int rc = configure_boxcar(map, maxw);
     if (rc) return rc;
     sps_stats_kernel<<<dim3((unsigned)a.nblk, (unsigned)a.ndm), 256, 0, stream>>>(a.dmt, a.n_out, a.norm_block,
                                                                                 a.nblk, wl, m0s, coefs);
     if (cudaGetLastError() != cudaSuccess) return SP_ECUDA;
+    if (cudaMemsetAsync(wide_count, 0, sizeof(int), stream) != cudaSuccess) return SP_ECUDA;
+    if (!map && cudaMemsetAsync(a.count, 0, sizeof(int64_t), stream) != cudaSuccess) return SP_ECUDA;
 
+    BoxcarArgs b;
+    b.dmt = a.dmt;
+    b.ndm = a.ndm;
+    b.n_out = a.n_out;
+    b.wl = wl;
+    b.maxw = maxw;
+    b.thr = a.threshold;
+    b.norm_block = a.norm_block;
+    b.nblk = a.nblk;
+    b.m0s = m0s;
+    b.coefs = coefs;
+    b.cands = a.cands;
+    b.cap = a.cap;
+    b.count = reinterpret_cast<unsigned long long *>(a.count);
+    b.map_best = a.map_best;
+    b.map_k = a.map_wbest;
+    b.wide_count = wide_count;
+    b.wide_list = wide_list;
+    b.vec = (a.n_out & 3) == 0 && (reinterpret_cast<uintptr_t>(a.dmt) & 15) == 0;
     const dim3 grid((unsigned)((a.n_out + kBxT - 1) / kBxT), (unsigned)((a.ndm + kBxIn - 1) / kBxIn));
+    int nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+        cudaGetLastError();
+        return SP_ECUDA;
+    }
     if (map) {
-        sps_boxcar_kernel<true><<<grid, 256, smem, stream>>>(a.dmt, a.ndm, a.n_out, wl, maxw, a.threshold,
-                                                             a.norm_block, a.nblk, m0s, coefs, nullptr, 0,
-                                                             nullptr, a.map_best, a.map_wbest);
+        sps_boxcar_kernel<true><<<grid, 256, boxcar_smem(maxw), stream>>>(b);
+        sps_boxcar_wide_kernel<true><<<nsm, 256, boxcar_wide_smem(maxw), stream>>>(b);
     } else {
-        if (cudaMemsetAsync(a.count, 0, sizeof(int64_t), stream) != cudaSuccess) return SP_ECUDA;
-        sps_boxcar_kernel<false><<<grid, 256, smem, stream>>>(
-            a.dmt, a.ndm, a.n_out, wl, maxw, a.threshold, a.norm_block, a.nblk, m0s, coefs, a.cands, a.cap,
-            reinterpret_cast<unsigned long long *>(a.count), nullptr, nullptr);
+        sps_boxcar_kernel<false><<<grid, 256, boxcar_smem(maxw), stream>>>(b);
+        sps_boxcar_wide_kernel<false><<<nsm, 256, boxcar_wide_smem(maxw), stream>>>(b);
     }
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }

@@ -43,7 +43,8 @@ def test_strerror(lib):
 
 
 def test_workspace_sizes(lib):
-    assert lib.sp_sps_workspace_bytes(501, 8192, 6, 8192) == 2048 + 24064
+    # m0 per (row, block), 9 coefficients per (row, block), the 64-bit tile list (32 x 36 tiles)
+    assert lib.sp_sps_workspace_bytes(501, 8192, 6, 8192) == 2048 + 24064 + 256 + 9216
     assert lib.sp_sps_workspace_bytes(0, 10, 1, 0) == -1
 
 

@@ -218,7 +218,29 @@ __device__ __forceinline__ void score_pass(const PT *Q, int d, int64_t s0, int64
         const int64_t t_lo = s0 + kBxFirst + l + 16 * (j0 + jlo), t_hi = s0 + kBxFirst + l + 16 * (j0 + jhi);
         const int64_t b_lo = block_of(t_lo, norm_block, nblk), b_hi = block_of(t_hi, norm_block, nblk);
         const int64_t row_blk = (int64_t)d * nblk;
-        if (b_lo == b_hi) {  // one normalisation block: coefficients once per width
+        const int i_last = kBxFirst + l + 16 * (j0 + jhi);
+        if (b_lo == b_hi && jlo == 0 && jhi == kBxPass - 1 && i_last + wl.w[wl.nw - 1] <= fit_end) {
+            // every point valid, every window inside the beam, one block
+            const PT m0 = (PT)(int64_t)__ldg(m0s + row_blk + b_lo);
+            PT q0[kBxPass];
+#pragma unroll
+            for (int j = 0; j < kBxPass; ++j) q0[j] = Q[kBxFirst + l + 16 * (j0 + j) - 1];
+            for (int k = 0; k < wl.nw; ++k) {
+                const int w = wl.w[k];
+                const PT cw = (PT)w * m0;
+                const float2 cf = __ldg(coefs + (row_blk + b_lo) * wl.nw + k);
+#pragma unroll
+                for (int j = 0; j < kBxPass; ++j) {
+                    const PT xs = Q[kBxFirst + l + 16 * (j0 + j) + w - 1] - q0[j] - cw;
+                    const float xf = sizeof(PT) == 4 ? (float)(int32_t)xs : (float)(int64_t)xs;
+                    const float sv = fmaf(xf, cf.x, -cf.y);
+                    if (sv > best[j]) {
+                        best[j] = sv;
+                        kb[j] = k;
+                    }
+                }
+            }
+        } else if (b_lo == b_hi) {  // one normalisation block: coefficients once per width
             const PT m0 = (PT)(int64_t)__ldg(m0s + row_blk + b_lo);
             for (int k = 0; k < wl.nw; ++k) {
                 const int w = wl.w[k];

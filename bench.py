@@ -516,7 +516,11 @@ def run_stream(args):
                                    1.0, 16.0, 8.0, 30.0)
         x = synth.make_beam((rng_seed, i), nchan, gulp, freqs, bursts, widths=widths)
         pool.append(torch.from_numpy(x).pin_memory())
-    hist = torch.from_numpy(synth.make_beam((rng_seed, 99), nchan, plan.max_delay, freqs)).pin_memory()
+    # The shared history holds two bursts (DM <= 1000, sweeps inside it) that
+    # every beam's first searched gulp covers.
+    hb = synth.draw_bursts(np.random.default_rng((rng_seed, 98)), 2, gulp, 300.0, 1000.0, 2.0, 16.0, 15.0, 30.0)
+    hist = torch.from_numpy(synth.make_beam((rng_seed, 99), nchan, plan.max_delay, freqs, hb,
+                                            widths=widths)).pin_memory()
     budget = int(args.dmt_budget_gb * (1 << 30)) + nbeams * (gulp + plan.max_delay) * nchan
     adds_per_gulp = float(nchan) * plan.ndm * gulp
 

@@ -53,7 +53,6 @@ struct sp_cnn {
     __nv_bfloat16 *dzT = nullptr, *colsT = nullptr, *wT = nullptr;
     float *dcols = nullptr, *prob = nullptr, *loss = nullptr;
     int64_t step = 0;
-    int32_t fwd_batch = 0;  // batch of the last forward with labels (for backward)
     bool have_grads = false;
 };
 

@@ -1,5 +1,5 @@
 // cnn.cu -- kernels of the candidate classifier (arXiv 2606.27262,
-// Sec. 3.2.2: a CNN judges each sifted candidate from two images, its
+// Sec. 3.2.2: a CNN scores each sifted candidate from two images, its
 // dedispersed dynamic spectrum and its DM transform; two networks, one per
 // image, fused multiplicatively into one probability).
 //

@@ -10,7 +10,8 @@ input (721 MB) and the DM transform (3.0 GB) are larger than the 129 MB L2,
 so no L2 flush is needed between steps.
 
   value   real-time beams = ranks * (131072 * 1.31072 ms) / device time per step
-          (input staging + dedispersion + block statistics + boxcar/peaks), inputs
+          (input staging + dedispersion + block statistics + boxcar/peaks + the 64-bit
+          boxcar pass over tiles the 32-bit pass could not prove exact), inputs
           resident in HBM.
   e2e     the same metric through sp_searcher_run_host: pinned host input
           copied in, candidates copied out, every step.
@@ -63,7 +64,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "real-time beams per GB300; dedispersion G(chan·DM·samp)/s vs roofline"
 MAX_SM_MHZ = 2070.0  # GB300 maximum SM clock
-KERNELS_PER_STEP = 4  # input staging, dedisperse, block statistics, boxcar/peaks
+KERNELS_PER_STEP = 5  # staging, dedispersion, block statistics, boxcar/peaks, 64-bit boxcar pass
 PROFILE_JSON = os.path.join(ROOT, "profiles", "dedisperse_config2_traffic.json")
 DEDISP_SRC = os.path.join(ROOT, "paper_2606_27262_gb300", "csrc", "dedisperse.cu")
 

@@ -472,7 +472,7 @@ def run_batched(args):
                      "peak_basis": f"{nsm} SMs x {lanes:.1f} measured 32-bit add lanes/SM/clk x "
                                    f"{MAX_SM_MHZ:.0f} MHz"},
         "e2e": None, "cpu_baseline": cpu, "clocks": clk,
-        "gpu_launches": (2 * bw.nbeams + bw.nbeams + ngroups) * args.steps,
+        "gpu_launches": (4 * bw.nbeams + ngroups) * args.steps,  # per beam: staging, statistics, boxcar, 64-bit pass; per group: dedispersion
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -17,8 +17,8 @@
  *     work is enqueued on it and the call returns without waiting, except
  *     where a call says it synchronises.  Buffers must stay valid until the
  *     stream has executed the work.
- *   - Only the create calls, the autotuner and sp_cnn_extract allocate
- *     device memory; the other calls allocate nothing.  Calls on different streams may overlap
+ *   - Only the create calls and the autotuner allocate device memory; the
+ *     other calls allocate nothing.  Calls on different streams may overlap
  *     as long as they do not share output or workspace buffers.
  *   - Filterbank layout: uint8 [n_in][nchan], time-major (the order a
  *     filterbank file or ring block stores samples), channel 0 = the highest
@@ -501,8 +501,8 @@ int sp_dmt_shifts(const double *freqs_mhz, int32_t nchan, int32_t nsub, int32_t 
  * (samples outside [0, n_in) count 0): each subband dedispersed at the
  * candidate's DM by Eq. 1's delays.  d_cands [ncand] device sp_cand;
  * d_sub fp32 [ncand][256][t_in] device; nchan a multiple of 256;
- * ncand <= 65535, t_in <= 4096.  Synchronises `stream` (it allocates and
- * frees a small table).  Errors: SP_EINVAL, SP_ENOMEM, SP_ECUDA. */
+ * ncand <= 65535, t_in <= 4096; every candidate's width_idx < nw.
+ * Asynchronous.  Errors: SP_EINVAL, SP_ECUDA. */
 int sp_cnn_extract(const sp_plan *plan, const uint8_t *d_staged, int64_t pitch, int64_t n_in,
                    const sp_cand *d_cands, int32_t ncand, const int32_t *h_widths, int32_t nw,
                    int32_t t_in, float *d_sub, void *stream);

@@ -434,27 +434,15 @@ extern "C" int sp_cnn_extract(const sp_plan *plan, const uint8_t *d_staged, int6
                               int32_t t_in, float *d_sub, void *stream) {
     if (!plan || !d_staged || !d_cands || ncand < 1 || ncand > 65535 || !d_sub || t_in < 1 || t_in > 4096)
         return SP_EINVAL;
-    int rc = check_widths(h_widths, nw);
+    const int rc = check_widths(h_widths, nw);
     if (rc) return rc;
     if (!on_plan_device(plan) || plan->nchan % kImg || pitch < dedisp_pitch(n_in) || n_in <= 0) return SP_EINVAL;
-    int32_t tab[2 * SP_MAX_WIDTHS];
-    for (int k = 0; k < nw; ++k) {
-        tab[k] = std::max(1, h_widths[k] / 4);
-        tab[SP_MAX_WIDTHS + k] = h_widths[k] / 2;
+    ExtractWidths wt;
+    for (int k = 0; k < SP_MAX_WIDTHS; ++k) {
+        const int32_t w = h_widths[std::min(k, nw - 1)];
+        wt.dec[k] = std::max(1, w / 4);
+        wt.half[k] = w / 2;
     }
-    // The two small tables travel in a device buffer owned by the plan's
-    // device for the duration of the call.
-    int32_t *d_tab = nullptr;
-    if (cudaMalloc((void **)&d_tab, sizeof tab) != cudaSuccess) {
-        cudaGetLastError();
-        return SP_ENOMEM;
-    }
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    rc = cudaMemcpyAsync(d_tab, tab, sizeof tab, cudaMemcpyHostToDevice, st) == cudaSuccess ? SP_OK : SP_ECUDA;
-    if (!rc)
-        rc = cnn_extract(d_staged, pitch, n_in, plan->nchan, plan->d_delays, d_cands, ncand, d_tab,
-                         d_tab + SP_MAX_WIDTHS, kImg, t_in, d_sub, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = SP_ECUDA;
-    cudaFree(d_tab);
-    return rc;
+    return cnn_extract(d_staged, pitch, n_in, plan->nchan, plan->d_delays, d_cands, ncand, wt, kImg, t_in, d_sub,
+                       reinterpret_cast<cudaStream_t>(stream));
 }

@@ -398,13 +398,13 @@ __global__ void normalise_kernel(const float *__restrict__ raw, __nv_bfloat16 *_
 // One CTA per (candidate, subband), threads over time bins.
 __global__ void extract_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int64_t n_in, int32_t nchan,
                                const int32_t *__restrict__ delays, const sp_cand *__restrict__ cands,
-                               const int32_t *__restrict__ dec_of_width, const int32_t *__restrict__ half_of_width,
-                               int32_t nsub, int32_t t_in, float *__restrict__ sub) {
+                               ExtractWidths wt, int32_t nsub, int32_t t_in, float *__restrict__ sub) {
     const int q = blockIdx.y, s = blockIdx.x;
     const sp_cand c = cands[q];
     const int per = nchan / nsub;
-    const int dec = dec_of_width[c.width_idx];
-    const int64_t t0 = (int64_t)c.t + half_of_width[c.width_idx];
+    const int wi = min(max(c.width_idx, 0), SP_MAX_WIDTHS - 1);
+    const int dec = wt.dec[wi];
+    const int64_t t0 = (int64_t)c.t + wt.half[wi];
     const int32_t *dl = delays + (int64_t)c.dm_idx * nchan;
     for (int u = threadIdx.x; u < t_in; u += blockDim.x) {
         const int64_t tb = t0 + (int64_t)(u - t_in / 2) * dec;
@@ -510,10 +510,10 @@ int cnn_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b, cudaStream_t st) {
 }
 
 int cnn_extract(const uint8_t *xt, int64_t pitch, int64_t n_in, int32_t nchan, const int32_t *delays,
-                const sp_cand *cands, int32_t ncand, const int32_t *dec_of_width, const int32_t *half_of_width,
-                int32_t nsub, int32_t t_in, float *sub, cudaStream_t st) {
-    extract_kernel<<<dim3((unsigned)nsub, (unsigned)ncand), 256, 0, st>>>(xt, pitch, n_in, nchan, delays, cands,
-                                                                        dec_of_width, half_of_width, nsub, t_in, sub);
+                const sp_cand *cands, int32_t ncand, const ExtractWidths &wt, int32_t nsub, int32_t t_in, float *sub,
+                cudaStream_t st) {
+    extract_kernel<<<dim3((unsigned)nsub, (unsigned)ncand), 256, 0, st>>>(xt, pitch, n_in, nchan, delays, cands, wt,
+                                                                        nsub, t_in, sub);
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

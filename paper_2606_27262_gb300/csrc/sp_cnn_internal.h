@@ -33,9 +33,14 @@ int cnn_bias_grad(const __nv_bfloat16 *dz, int64_t P, int C, float *db, cudaStre
 int cnn_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
              int64_t step, __nv_bfloat16 *wb, cudaStream_t st);
 int cnn_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b, cudaStream_t st);
+// Decimation and half width of each trial width, passed by value.
+struct ExtractWidths {
+    int32_t dec[SP_MAX_WIDTHS];
+    int32_t half[SP_MAX_WIDTHS];
+};
 int cnn_extract(const uint8_t *xt, int64_t pitch, int64_t n_in, int32_t nchan, const int32_t *delays,
-                const sp_cand *cands, int32_t ncand, const int32_t *dec_of_width, const int32_t *half_of_width,
-                int32_t nsub, int32_t t_in, float *sub, cudaStream_t st);
+                const sp_cand *cands, int32_t ncand, const ExtractWidths &wt, int32_t nsub, int32_t t_in, float *sub,
+                cudaStream_t st);
 int cnn_features(const float *sub, int Nb, int S, int T_in, const int32_t *shift, float *ft_raw, float *dmt_raw,
                  __nv_bfloat16 *ft, __nv_bfloat16 *dmt, cudaStream_t st);
 

@@ -36,10 +36,13 @@ per second, next to the same work as per-beam launches (also a graph).
 `--workload stream` measures the streaming server: 256 beams of 4096
 channels arriving as 8.0 s gulps (6104 samples) overlapped by the DM-2000
 sweep (5751 trials), device rings and slots admitted by an HBM budget,
-continuous batching.  value = sustained real-time beams (gulps searched per
-second at saturation x 8.0 s), next to per-gulp launches on one stream; the
-p50/p99 latency of real-time arrivals for the 256 beams is reported against
-the 8.0 s deadline.
+continuous batching, each gulp's candidates sifted on the host and the kept
+peaks scored by the classifier inside the stream.  value = sustained
+real-time beams (gulps finished per second at saturation x 8.0 s), next to
+the same stream without sifter and classifier and to per-gulp launches on
+one stream with the plain sifter; the p50/p99 latency of real-time arrivals
+for the 256 beams through the whole chain is reported against the 8.0 s
+deadline.
 
 `--workload classifier` measures the candidate classifier: training steps
 (features + forward + backward + Adam, batch 64) and inference (features +
@@ -517,65 +520,104 @@ def run_stream(args):
                                    1.0, 16.0, 8.0, 30.0)
         x = synth.make_beam((rng_seed, i), nchan, gulp, freqs, bursts, widths=widths)
         pool.append(torch.from_numpy(x).pin_memory())
-    # The shared history holds two bursts (DM <= 1000, sweeps inside it) that
-    # every beam's first searched gulp covers.
-    hb = synth.draw_bursts(np.random.default_rng((rng_seed, 98)), 2, gulp, 300.0, 1000.0, 2.0, 16.0, 15.0, 30.0)
+    # The shared history (the first max_delay samples, which the first
+    # searched windows cover) holds one burst per gulp-long segment whose
+    # sweep fits inside it (DM <= 1000, and lower late in the history), so
+    # that every gulp searched in a short run has a burst for the sifter
+    # and the classifier.
+    hrng = np.random.default_rng((rng_seed, 98))
+    per_dm = float(synth.fractional_delay(freqs, 1.0)[-1])
+    hb = []
+    for j in range(plan.max_delay // gulp):
+        t0 = j * gulp + int(hrng.integers(64, gulp - 128))
+        dm_hi = min(1000.0, (plan.max_delay - t0 - 256) / per_dm)
+        if dm_hi < 60.0:
+            break
+        hb.append(synth.Burst(t0, float(hrng.uniform(50.0, dm_hi)), float(hrng.uniform(2.0, 16.0)),
+                              float(hrng.uniform(15.0, 30.0))))
     hist = torch.from_numpy(synth.make_beam((rng_seed, 99), nchan, plan.max_delay, freqs, hb,
                                             widths=widths)).pin_memory()
     budget = int(args.dmt_budget_gb * (1 << 30)) + nbeams * (gulp + plan.max_delay) * nchan
     adds_per_gulp = float(nchan) * plan.ndm * gulp
 
-    def saturated(flags, max_batch, rounds=2):
+    # The classifier of the full chain: random-init weights (its cost does
+    # not depend on them; the trained network's recall is a test result).
+    clf = sp.Classifier(max_batch=64, seed=5)
+    t_in, kept_cap = 512, 64
+
+    def make_stream(flags, max_batch, stage):
         s = sp.Stream(plan, nbeams, gulp, widths, 6.0, 8192, cap, budget, max_batch=max_batch, flags=flags)
+        if stage is not None:
+            s.attach(clf if stage == "classify" else None, t_in=t_in, kept_cap=kept_cap)
         for b in range(nbeams):
             s.history(b, hist)
+        return s
+
+    def saturated(flags, max_batch, stage, rounds=2):
+        s = make_stream(flags, max_batch, stage)
         k = 0
+        tally = [0, 0, 0]  # candidates, kept, accepted
+
+        def poll(wait=False):
+            res = (s.drain(with_cands=False, sifted=True) if wait else s.poll_sifted()) if stage is not None \
+                else (s.drain(with_cands=False) if wait else s.poll(with_cands=False))
+            for r in res:
+                tally[0] += int(r[0].count)
+                tally[1] += int(r[0].kept)
+                tally[2] += int(r[0].accepted)
 
         def one_round():
             nonlocal k
             for b in range(nbeams):
                 s.push(b, pool[(3 * b + k) % len(pool)])
-                s.poll(with_cands=False)
+                poll()
             k += 1
         one_round()
-        s.drain(with_cands=False)  # warm-up round
+        poll(wait=True)  # warm-up round
+        tally[:] = [0, 0, 0]
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(rounds):
             one_round()
-        s.drain(with_cands=False)
+        poll(wait=True)
         dt = reduce_max(time.perf_counter() - t0, world, dev)
-        info = {"slots": s.slots, "device_bytes": s.device_bytes}
+        info = {"slots": s.slots, "device_bytes": s.device_bytes, "candidates": tally[0], "kept": tally[1],
+                "accepted": tally[2]}
         s.close()
         return rounds * nbeams / dt, dt, info
 
-    rate_b, dt_b, info_b = saturated(0, 16)
-    rate_p, dt_p, info_p = saturated(sp.SP_STREAM_PER_GULP | sp.SP_STREAM_ONE_STREAM, 1)
+    rate_b, dt_b, info_b = saturated(0, 16, "classify")
+    rate_s, dt_s, info_s = saturated(0, 16, None)
+    rate_p, dt_p, info_p = saturated(sp.SP_STREAM_PER_GULP | sp.SP_STREAM_ONE_STREAM, 1, "sift")
+    rate_q, dt_q, info_q = saturated(sp.SP_STREAM_PER_GULP | sp.SP_STREAM_ONE_STREAM, 1, None)
 
     # Real-time arrivals: every beam pushes a gulp each period, beams
-    # staggered evenly over the period.
-    s = sp.Stream(plan, nbeams, gulp, widths, 6.0, 8192, cap, budget, max_batch=16)
-    for b in range(nbeams):
-        s.history(b, hist)
-    lat, cand_total = [], 0
+    # staggered evenly over the period; the full chain (search, sifter,
+    # classifier) is attached.
+    s = make_stream(0, 16, "classify")
+    lat, lat_search, cand_total, kept_total = [], [], 0, 0
     nper = max(1, int(round(args.stream_periods)))
     arrivals = sorted((k * period + b * period / nbeams, b, k) for k in range(nper) for b in range(nbeams))
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     t_start = sp.stream_now() + 0.05
+    def record(res):
+        nonlocal cand_total, kept_total
+        for r, _, _, _ in res:
+            lat.append(r.t_done - r.t_push)
+            lat_search.append(r.t_search - r.t_push)
+            cand_total += int(r.count)
+            kept_total += int(r.kept)
     for ta, b, k in arrivals:
         while sp.stream_now() < t_start + ta:
-            for r, _ in s.poll(with_cands=False):
-                lat.append(r.t_done - r.t_push)
-                cand_total += int(r.count)
+            record(s.poll_sifted())
             time.sleep(0.0005)
         s.push(b, pool[(3 * b + k) % len(pool)])
-    for r, _ in s.drain(with_cands=False):
-        lat.append(r.t_done - r.t_push)
-        cand_total += int(r.count)
+    record(s.drain(with_cands=False, sifted=True))
     clk = clocks.stop()
     s.close()
-    lat = np.array(lat)
+    clf.close()
+    lat, lat_search = np.array(lat), np.array(lat_search)
     lines = {
         "metric": METRIC, "value": world * rate_b * period, "unit": "beams", "n_gpus": world,
         "steps": 2 * nbeams, "warmup": nbeams, "ms_per_step": 1e3 / rate_b, "higher_is_better": True,
@@ -586,20 +628,37 @@ def run_stream(args):
                                f"{plan.max_delay} samples), widths 1-256",
                    "gulp": gulp, "n_in": gulp + plan.max_delay, "ndm": plan.ndm, "max_batch": 16,
                    "hbm_budget_bytes": budget, "slots": info_b["slots"], "device_bytes": info_b["device_bytes"],
-                   "step": "one gulp (value = gulps searched per second at saturation x gulp duration)",
+                   "step": "one gulp through search, sifter and classifier (value = gulps finished per second "
+                           "at saturation x gulp duration)",
+                   "chain": f"batched dedispersion (one CTA per work item while a classifier is attached), "
+                            f"search on a high-priority stream, host DBSCAN sifter (Sec. 3.2.1 defaults), "
+                            f"classifier on the kept peaks of each finished batch on a high-priority stream "
+                            f"(t_in {t_in}, up to {kept_cap} per gulp, random-init weights: throughput only)",
                    "l2": "rings and windows larger than L2, no flush", "parallelism": f"replicas x{world}"},
+        "sifted": {"candidates": info_b["candidates"], "kept": info_b["kept"], "classified": info_b["kept"],
+                   "gulps": 2 * nbeams},
+        "search_only": {"value": world * rate_s * period, "unit": "beams", "ms_per_gulp": 1e3 / rate_s,
+                        "candidates": info_s["candidates"], "launches": "batched, no sifter or classifier attached"},
         "per_gulp": {"value": world * rate_p * period, "unit": "beams", "ms_per_gulp": 1e3 / rate_p,
-                     "launches": "each gulp: copy, stage, dedisperse (grid kernel), search; one stream"},
+                     "candidates": info_p["candidates"], "kept": info_p["kept"],
+                     "launches": "each gulp: copy, stage, dedisperse (grid kernel), search, plain sifter; "
+                                 "one stream"},
+        "per_gulp_search_only": {"value": world * rate_q * period, "unit": "beams", "ms_per_gulp": 1e3 / rate_q,
+                                 "launches": "as per_gulp, without the sifter"},
         "speedup_vs_per_gulp": rate_b / rate_p,
         "latency": {"beams": nbeams, "periods": nper, "gulps": int(lat.size), "deadline_s": period,
                     "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                     "max_s": float(lat.max()), "met_deadline": bool(lat.max() < period),
-                    "candidates": cand_total},
+                    "search_p50_s": float(np.percentile(lat_search, 50)),
+                    "search_p99_s": float(np.percentile(lat_search, 99)),
+                    "candidates": cand_total, "kept": kept_total},
         "roofline": {"bound": "alu", "achieved": adds_per_gulp * rate_b / 1e12, "unit": "Tadd/s",
-                     "kernel": "whole streaming path at saturation (copies, staging, dedispersion, search)",
+                     "kernel": "whole streaming chain at saturation (copies, staging, dedispersion, search, sifter, "
+                               "classifier)",
                      "peak": None, "frac": None, "traffic": None},
         "e2e": {"value": world * rate_b * period, "unit": "beams", "h2d_bytes_per_step": gulp * nchan,
-                "d2h_bytes_per_step": 8 + 16 * cap, "api": "sp_stream_push / sp_stream_poll from pinned host gulps"},
+                "d2h_bytes_per_step": 8 + 16 * cap + 4 * kept_cap,
+                "api": "sp_stream_push / sp_stream_poll_sifted from pinned host gulps"},
         "cpu_baseline": None, "clocks": clk,
         "gpu_launches": None,
     }

@@ -522,7 +522,9 @@ int sp_cnn_extract(const sp_plan *plan, const uint8_t *d_staged, int64_t pitch, 
  * Device memory: one ring per beam holding the last n_in samples (uint8,
  * time-major), then as many in-flight slots (staged window, DM transform,
  * search scratch, candidates) as fit in hbm_budget_bytes beside the rings,
- * at most max_batch per launch stream.  SP_ENOMEM if not even one fits.
+ * at most max_batch per launch stream plus max_batch more (so that a batch
+ * can be admitted while an earlier batch's slots are still held by its
+ * classification).  SP_ENOMEM if not even one fits.
  * Scheduling (continuous batching): pushed gulps wait in a FIFO.  Whenever
  * a launch stream and slots are free, the oldest pending gulps (at most
  * max_batch) form a batch: each gulp is copied into its ring (after the
@@ -551,11 +553,39 @@ int sp_cnn_extract(const sp_plan *plan, const uint8_t *d_staged, int64_t pitch, 
  * sp_gulp_result: beam, seq, t0 = seq * gulp (first searched sample of the
  *   window in the beam's output time), count (total candidates; only
  *   min(count, cand_cap) are returned; status SP_EOVERFLOW when it exceeds),
- *   t_push and t_done (host seconds: arrival, and when the gulp's results
- *   were on the host).
- * sp_stream_pending: gulps queued, in flight and finished-but-not-polled.
+ *   t_push and t_done (host seconds: arrival, and when all of the gulp's
+ *   results were on the host), t_search (when its search candidates were;
+ *   = t_done without sp_stream_attach), kept and accepted (below; 0
+ *   without sp_stream_attach).
+ * sp_stream_pending: gulps queued, in flight (searching or classifying) and
+ *   finished-but-not-polled.
  * sp_stream_info: slot count, device bytes held, window length n_in.
- * sp_stream_now: the clock of t_push / t_done (seconds, monotonic). */
+ * sp_stream_now: the clock of t_push / t_done (seconds, monotonic).
+ *
+ * Sifting and classification in the stream (Sec. 3.2: each searched block's
+ * candidates are clustered and thresholded, and the surviving cluster peaks
+ * are scored by the classifier before the block's results are final).
+ * sp_stream_attach: from now on each finished gulp's candidates are sifted
+ *   on the host (sp_sift with *params, the gulp's candidates as returned);
+ *   with clf != NULL the kept peaks (the first kept_cap in (dm_idx, t)
+ *   order) are then cut from the gulp's staged window (sp_cnn_extract,
+ *   t_in bins), made into images (sp_cnn_features with the sp_dmt_shifts
+ *   table of sweep (t_in - 256) / 2) and scored (sp_cnn_forward) on a
+ *   high-priority stream of the library's own while later gulps are
+ *   searched; the peaks of all gulps of one finished batch are imaged and
+ *   scored together (up to SP_CNN_MAX_BATCH per job).  The gulp's slot is
+ *   reused only after its classification has finished, and its result is
+ *   returned once the probabilities are on the host.  clf must outlive the
+ *   stream and must not run on another stream meanwhile.  With clf: nchan
+ *   a multiple of 256, 256 <= t_in <= 4096, t_in even.  1 <= kept_cap <=
+ *   SP_CNN_MAX_BATCH.  Allowed once, before the first push (SP_EINVAL
+ *   otherwise).
+ * sp_stream_poll_sifted: sp_stream_poll, plus per result i its kept peaks
+ *   in kept + i * kept_cap and their probabilities p in prob + i * kept_cap
+ *   (-1 without a classifier); either may be NULL.  Result fields: kept =
+ *   total peaks the sifter kept (status SP_EOVERFLOW when above kept_cap);
+ *   accepted = how many of the returned ones have p >= 0.5 (all of them
+ *   without a classifier). */
 typedef struct sp_stream sp_stream;
 typedef struct {
     int32_t beam;
@@ -565,6 +595,9 @@ typedef struct {
     int64_t count;
     double t_push;
     double t_done;
+    double t_search;
+    int64_t kept;
+    int64_t accepted;
 } sp_gulp_result;
 #define SP_STREAM_PER_GULP 1
 #define SP_STREAM_ONE_STREAM 2
@@ -579,6 +612,9 @@ int sp_stream_poll(sp_stream *s, int32_t wait, sp_gulp_result *out, sp_cand *can
                    int32_t max_results, int32_t *n_results);
 int sp_stream_pending(const sp_stream *s, int64_t *queued, int64_t *in_flight, int64_t *ready);
 double sp_stream_now(void);
+int sp_stream_attach(sp_stream *s, const sp_sift_params *params, sp_cnn *clf, int32_t t_in, int32_t kept_cap);
+int sp_stream_poll_sifted(sp_stream *s, int32_t wait, sp_gulp_result *out, sp_cand *cands, sp_cand *kept,
+                          float *prob, int32_t max_results, int32_t *n_results);
 
 #ifdef __cplusplus
 }

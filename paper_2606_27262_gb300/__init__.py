@@ -97,6 +97,8 @@ SIGNATURES = {
     "sp_stream_poll": (ctypes.c_int, [P, I32, P, P, I32, P]),
     "sp_stream_pending": (ctypes.c_int, [P, P, P, P]),
     "sp_stream_now": (F64, []),
+    "sp_stream_attach": (ctypes.c_int, [P, P, P, I32, I32]),
+    "sp_stream_poll_sifted": (ctypes.c_int, [P, I32, P, P, P, P, I32, P]),
     "sp_sift": (ctypes.c_int, [P, I64, P, I32, P, I32, F64, P, P, I64, P, P]),
     "sp_inject_quantised": (ctypes.c_int, [P, P, I64, I32, F64, F64, F64, P]),
     "sp_cnn_num_params": (I64, []),
@@ -526,7 +528,8 @@ class Batch:
 class GulpResult(ctypes.Structure):
     _fields_ = [("beam", ctypes.c_int32), ("status", ctypes.c_int32), ("seq", ctypes.c_int64),
                 ("t0", ctypes.c_int64), ("count", ctypes.c_int64), ("t_push", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("t_search", ctypes.c_double), ("kept", ctypes.c_int64),
+                ("accepted", ctypes.c_int64)]
 
 
 def stream_now() -> float:
@@ -551,6 +554,25 @@ class Stream:
         _check(_lib().sp_stream_info(h, ctypes.byref(sl), ctypes.byref(nb), ctypes.byref(ni)), "sp_stream_info")
         self.slots, self.device_bytes, self.n_in = int(sl.value), int(nb.value), int(ni.value)
         self._keep = {}  # host buffers referenced by gulps not yet returned
+        self.kept_cap = 0
+        self._clf = None
+
+    def attach(self, clf=None, t_in: int = 512, kept_cap: int = 64, **sift_params):
+        """Sifts every finished gulp (sp_sift, SIFT_DEFAULTS updated by
+        sift_params) and, with a Classifier, scores the kept peaks from the
+        gulp's staged window (sp_stream_attach); results then come from
+        poll_sifted."""
+        p = dict(SIFT_DEFAULTS)
+        p.update(sift_params)
+        sp_p = SiftParams(float(p["eps"]), int(p["min_points"]), float(p["snr_min"]), float(p["dm_min"]),
+                          float(p["width_max_s"]))
+        _check(_lib().sp_stream_attach(self._h, ctypes.byref(sp_p), clf._h if clf is not None else None,
+                                       int(t_in), int(kept_cap)), "sp_stream_attach")
+        self.kept_cap = int(kept_cap)
+        self._clf = clf  # must outlive the stream
+        device_bytes = ctypes.c_int64()
+        _check(_lib().sp_stream_info(self._h, None, ctypes.byref(device_bytes), None), "sp_stream_info")
+        self.device_bytes = int(device_bytes.value)
 
     def history(self, beam: int, h_hist):
         _check(_lib().sp_stream_history(self._h, int(beam), _ptr(h_hist)), "sp_stream_history")
@@ -584,17 +606,48 @@ class Stream:
             out.append((GulpResult.from_buffer_copy(r), c))
         return out
 
+    def poll_sifted(self, wait: bool = False, max_results: int = 64, with_cands: bool = False):
+        """Finished gulps after the attached sifter (and classifier): list of
+        (GulpResult, candidates or None, kept peaks structured array,
+        probabilities float32 (-1 without a classifier))."""
+        if getattr(self, "_sres_n", 0) < max_results:
+            self._sres = (GulpResult * max_results)()
+            self._skept = np.zeros((max_results * self.kept_cap, 4), np.int32)
+            self._sprob = np.zeros(max_results * self.kept_cap, np.float32)
+            self._sres_n = max_results
+        if with_cands and getattr(self, "_scand_n", 0) < max_results:
+            self._scands = np.zeros((max_results * self.cap, 4), np.int32)
+            self._scand_n = max_results
+        res, kept, prob = self._sres, self._skept, self._sprob
+        n = ctypes.c_int32()
+        _check(_lib().sp_stream_poll_sifted(self._h, int(bool(wait)), ctypes.cast(res, ctypes.c_void_p),
+                                            self._scands.ctypes.data if with_cands else None, kept.ctypes.data,
+                                            prob.ctypes.data, int(max_results), ctypes.byref(n)),
+               "sp_stream_poll_sifted")
+        out = []
+        for i in range(n.value):
+            r = res[i]
+            self._keep.pop((int(r.beam), int(r.seq)), None)
+            nk = min(int(r.kept), self.kept_cap)
+            c = (cands_to_numpy(self._scands[i * self.cap:(i + 1) * self.cap], min(int(r.count), self.cap))
+                 if with_cands else None)
+            k = kept[i * self.kept_cap:i * self.kept_cap + nk].copy().view(CAND_DTYPE).reshape(-1)
+            out.append((GulpResult.from_buffer_copy(r), c, k, prob[i * self.kept_cap:i * self.kept_cap + nk].copy()))
+        return out
+
     def pending(self):
         q, f, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(_lib().sp_stream_pending(self._h, ctypes.byref(q), ctypes.byref(f), ctypes.byref(r)),
                "sp_stream_pending")
         return int(q.value), int(f.value), int(r.value)
 
-    def drain(self, with_cands: bool = True):
-        """Polls (blocking) until nothing is queued or in flight."""
+    def drain(self, with_cands: bool = True, sifted: bool = False):
+        """Polls (blocking) until nothing is queued or in flight (poll_sifted
+        results when ``sifted``)."""
         out = []
         while True:
-            out += self.poll(wait=True, with_cands=with_cands)
+            out += (self.poll_sifted(wait=True, with_cands=with_cands) if sifted
+                    else self.poll(wait=True, with_cands=with_cands))
             q, f, r = self.pending()
             if q == 0 and f == 0 and r == 0:
                 return out

@@ -446,3 +446,8 @@ extern "C" int sp_cnn_extract(const sp_plan *plan, const uint8_t *d_staged, int6
     return cnn_extract(d_staged, pitch, n_in, plan->nchan, plan->d_delays, d_cands, ncand, wt, kImg, t_in, d_sub,
                        reinterpret_cast<cudaStream_t>(stream));
 }
+
+namespace sp {
+int32_t cnn_max_batch(const sp_cnn *c) { return c ? c->max_batch : 0; }
+int cnn_device(const sp_cnn *c) { return c ? c->device : -1; }
+}  // namespace sp

@@ -140,6 +140,8 @@ static int create_plan(const double *freqs_mhz, int32_t nchan, double tsamp_s, c
     p->nchan = nchan;
     p->ndm = ndm;
     p->tsamp = tsamp_s;
+    p->freqs.assign(freqs_mhz, freqs_mhz + nchan);
+    p->dms.assign(dms, dms + ndm);
     p->shape = shape;
     p->chan_chunk = kDedispShapeCh[shape];
     p->dm_tile = kDedispDmPerThread * p->chan_chunk;

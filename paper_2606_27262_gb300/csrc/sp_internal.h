@@ -52,6 +52,8 @@ struct sp_plan {
     int device = 0;
     int32_t nchan = 0, ndm = 0, max_delay = 0;
     double tsamp = 0.0;
+    std::vector<double> freqs;    // host copy of the channel axis [nchan] (MHz)
+    std::vector<double> dms;      // host copy of the trial DMs [ndm]
     std::vector<int32_t> delays;  // host copy [ndm][nchan]
     // Kernel shape (index into kDedispShapeCh/Spt) and its tile sizes.
     int32_t shape = 0;
@@ -155,5 +157,9 @@ inline int64_t align256(int64_t x) { return (x + 255) & ~int64_t(255); }
 // Argument checks shared by the entry points (capi.cpp).
 bool on_plan_device(const sp_plan *p);
 int check_widths(const int32_t *w, int32_t nw);
+
+// Facts about a classifier that the streaming search needs (cnn.cpp).
+int32_t cnn_max_batch(const sp_cnn *c);
+int cnn_device(const sp_cnn *c);
 
 }  // namespace sp

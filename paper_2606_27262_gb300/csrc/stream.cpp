@@ -12,11 +12,18 @@
 // candidates are copied back.  With two launch streams a new batch is
 // admitted while the previous one is still on the GPU (continuous batching).
 // No threads: all progress happens in sp_stream_push / sp_stream_poll.
+//
+// With a sifter (and classifier) attached, each finished gulp's candidates
+// are clustered on the host (sp_sift) and the kept peaks are scored from the
+// gulp's staged window on a classifier stream while later batches run; the
+// slot is recycled after that, and the result is returned when the scores
+// are on the host (Sec. 3.2: sifting and classification of each block).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -52,9 +59,11 @@ struct Slot {
 
 struct Launch {  // one batch in flight on one launch stream
     bool busy = false;
+    uint64_t order = 0;  // launches started before this one
     std::vector<Gulp> gulps;
     std::vector<int> slots;
     cudaEvent_t done = nullptr;
+    cudaEvent_t dedispersed = nullptr;
     std::atomic<int> finished{0};
     double t_done = 0.0;
     BatchBeamDev *h_table = nullptr;  // pinned [max_batch]
@@ -73,7 +82,36 @@ void CUDART_CB mark_done(void *p) {  // host callback: no CUDA calls here
 struct Result {
     sp_gulp_result info;
     std::vector<sp_cand> cands;
+    std::vector<sp_cand> kept;
+    std::vector<float> prob;
 };
+
+// Peaks scored by one classification job: the kept peaks of the gulps of
+// one finished batch, cut, imaged and scored together.
+constexpr int32_t kClsCap = SP_CNN_MAX_BATCH;
+
+struct Searched {  // a gulp whose candidates are on the host, not yet sifted
+    Result r;
+    int slot = 0;
+};
+
+struct JobRec {  // a classification job (FIFO on the classifier stream)
+    std::atomic<int> finished{0};  // set by a host callback after the scores' copy
+    double t_done = 0.0;
+    cudaEvent_t done = nullptr;
+    sp_cand *h_kept = nullptr;     // pinned [kClsCap]
+    float *h_prob = nullptr;       // pinned [kClsCap]
+    std::vector<Result> rs;        // the gulps it scores, their slots and first peaks
+    std::vector<int> slots;
+    std::vector<int32_t> first;
+    int32_t total = 0;
+};
+
+void CUDART_CB mark_classified(void *p) {  // host callback: no CUDA calls here
+    JobRec *j = static_cast<JobRec *>(p);
+    j->t_done = now_s();
+    j->finished.store(1, std::memory_order_release);
+}
 
 }  // namespace
 
@@ -103,9 +141,34 @@ struct sp_stream {
     std::vector<int> free_slots;
     Launch launches[kMaxStreams];
     cudaStream_t streams[kMaxStreams] = {nullptr, nullptr};
+    // Searches and result copies of every batch (highest priority), unless
+    // SP_STREAM_ONE_STREAM keeps all of a batch on its launch stream.
+    cudaStream_t search_stream = nullptr;
     BatchLaunch geometry{};
     std::deque<Gulp> pending;
+    std::deque<Searched> searched;
     std::deque<Result> results;
+    uint64_t launches_started = 0;
+    bool pushed = false;
+    // sifting and classification (sp_stream_attach)
+    bool attached = false;
+    sp_sift_params sift{};
+    sp_cnn *clf = nullptr;
+    int32_t t_in = 0, kept_cap = 0;
+    cudaStream_t cls_stream = nullptr;
+    sp_cand *d_kept = nullptr;     // [kClsCap]
+    float *d_sub = nullptr;        // [kClsCap][256][t_in]
+    void *d_ft = nullptr;          // bf16 [kClsCap][256][256]
+    void *d_img = nullptr;         // bf16 [kClsCap][256][256] (DM-time)
+    void *d_work = nullptr;
+    int64_t work_bytes = 0;
+    int32_t *d_shift = nullptr;    // [256][256]
+    float *d_prob = nullptr;       // [kClsCap]
+    std::unique_ptr<JobRec[]> recs;  // [slots]: a job holds at least one slot
+    std::vector<int> free_recs;
+    std::deque<int> jobs;          // dispatched, in order
+    int open_job = -1;             // being filled
+    std::vector<sp_cand> sift_buf;
 };
 
 namespace {
@@ -134,6 +197,7 @@ void stream_free(sp_stream *s) {
     for (int i = 0; i < kMaxStreams; ++i) {
         Launch &l = s->launches[i];
         if (l.done) cudaEventDestroy(l.done);
+        if (l.dedispersed) cudaEventDestroy(l.dedispersed);
         cudaFreeHost(l.h_table);
         cudaFreeHost(l.h_begin);
         cudaFree(l.d_table);
@@ -150,9 +214,24 @@ void stream_free(sp_stream *s) {
         cudaFreeHost(sl.h_cands);
         cudaFreeHost(sl.h_count);
     }
+    for (size_t i = 0; s->recs && i < s->slots.size(); ++i) {
+        JobRec &j = s->recs[i];
+        cudaFreeHost(j.h_kept);
+        cudaFreeHost(j.h_prob);
+        if (j.done) cudaEventDestroy(j.done);
+    }
     for (cudaEvent_t e : s->staged_ev)
         if (e) cudaEventDestroy(e);
     cudaFree(s->d_rings);
+    if (s->search_stream) cudaStreamDestroy(s->search_stream);
+    if (s->cls_stream) cudaStreamDestroy(s->cls_stream);
+    cudaFree(s->d_kept);
+    cudaFree(s->d_sub);
+    cudaFree(s->d_ft);
+    cudaFree(s->d_img);
+    cudaFree(s->d_work);
+    cudaFree(s->d_shift);
+    cudaFree(s->d_prob);
 }
 
 int64_t slot_bytes(const sp_stream *s) {
@@ -263,21 +342,37 @@ int launch_batch(sp_stream *s, int li) {
         B.d_item_begin = L.d_begin;
         B.d_counter = L.d_counter;
         B.d_status = p->d_status;
-        if (!rc) rc = launch_dedisperse_batch(B, st, true);
+        // A persistent grid holds every SM until the batch is done, so the
+        // classifier's kernels could not start before then; with a
+        // classifier attached each item gets its own CTA, and the
+        // high-priority classifier CTAs take SMs as items retire.
+        if (!rc) rc = launch_dedisperse_batch(B, st, s->clf == nullptr);
+    }
+    // The searches go to the high-priority search stream: the next batch's
+    // dedispersion (already queued on the other launch stream) would
+    // otherwise take the SMs first and hold this batch's results back until
+    // it ends.
+    cudaStream_t ss = st;
+    if (!rc && s->search_stream) {
+        if (cudaEventRecord(L.dedispersed, st) != cudaSuccess ||
+            cudaStreamWaitEvent(s->search_stream, L.dedispersed, 0) != cudaSuccess)
+            rc = SP_ECUDA;
+        ss = s->search_stream;
     }
     for (int i = 0; i < n && !rc; ++i) {
         const Slot &sl = s->slots[L.slots[i]];
-        rc = search_slot(s, sl, st);
-        if (!rc && (cudaMemcpyAsync(sl.h_count, sl.d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st) !=
+        rc = search_slot(s, sl, ss);
+        if (!rc && (cudaMemcpyAsync(sl.h_count, sl.d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, ss) !=
                         cudaSuccess ||
                     cudaMemcpyAsync(sl.h_cands, sl.d_cands, (size_t)s->cap * sizeof(sp_cand),
-                                    cudaMemcpyDeviceToHost, st) != cudaSuccess))
+                                    cudaMemcpyDeviceToHost, ss) != cudaSuccess))
             rc = SP_ECUDA;
     }
     L.finished.store(0, std::memory_order_relaxed);
-    if (!rc && (cudaLaunchHostFunc(st, mark_done, &L) != cudaSuccess || cudaEventRecord(L.done, st) != cudaSuccess))
+    if (!rc && (cudaLaunchHostFunc(ss, mark_done, &L) != cudaSuccess || cudaEventRecord(L.done, ss) != cudaSuccess))
         rc = SP_ECUDA;
     L.busy = true;  // even on error: its slots return when the stream has drained
+    L.order = s->launches_started++;
     if (rc) {
         L.t_done = now_s();
         L.finished.store(1, std::memory_order_release);
@@ -285,8 +380,134 @@ int launch_batch(sp_stream *s, int li) {
     return rc;
 }
 
-// Collects finished launches, then starts new ones while possible.
+// Queues the open classification job on the classifier stream: each gulp's
+// peaks are cut from its own staged window, then all of them are imaged and
+// scored together and the scores copied back.  On failure its gulps are
+// finished with the error (after whatever was queued has drained).
+int dispatch_job(sp_stream *s) {
+    if (s->open_job < 0) return SP_OK;
+    const int id = s->open_job;
+    s->open_job = -1;
+    JobRec &j = s->recs[id];
+    const sp_plan *p = s->plan;
+    cudaStream_t st = s->cls_stream;
+    j.finished.store(0, std::memory_order_relaxed);
+    int rc = SP_OK;
+    if (cudaMemcpyAsync(s->d_kept, j.h_kept, (size_t)j.total * sizeof(sp_cand), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        rc = SP_ECUDA;
+    for (size_t g = 0; g < j.rs.size() && !rc; ++g)
+        rc = sp_cnn_extract(p, s->slots[(size_t)j.slots[g]].d_staged, s->pitch, s->n_in, s->d_kept + j.first[g],
+                            (int32_t)j.rs[g].kept.size(), s->widths, s->nw, s->t_in,
+                            s->d_sub + (int64_t)j.first[g] * 256 * s->t_in, st);
+    if (!rc)
+        rc = sp_cnn_features(s->d_sub, j.total, 256, s->t_in, s->d_shift, s->d_ft, s->d_img, s->d_work,
+                             s->work_bytes, st);
+    const int32_t bmax = cnn_max_batch(s->clf);
+    const int64_t img = (int64_t)256 * 256 * 2;  // bytes of one bf16 image
+    for (int32_t i = 0; i < j.total && !rc; i += bmax)
+        rc = sp_cnn_forward(s->clf, static_cast<uint8_t *>(s->d_ft) + i * img,
+                            static_cast<uint8_t *>(s->d_img) + i * img, std::min(bmax, j.total - i), s->d_prob + i,
+                            st);
+    if (!rc &&
+        (cudaMemcpyAsync(j.h_prob, s->d_prob, (size_t)j.total * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaLaunchHostFunc(st, mark_classified, &j) != cudaSuccess || cudaEventRecord(j.done, st) != cudaSuccess))
+        rc = SP_ECUDA;
+    if (!rc) {
+        s->jobs.push_back(id);
+        return SP_OK;
+    }
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    for (size_t g = 0; g < j.rs.size(); ++g) {
+        Result &r = j.rs[g];
+        r.info.status = rc;
+        r.prob.assign(r.kept.size(), -1.0f);
+        s->results.push_back(std::move(r));
+        s->free_slots.push_back(j.slots[g]);
+    }
+    j.rs.clear();
+    j.slots.clear();
+    j.first.clear();
+    j.total = 0;
+    s->free_recs.push_back(id);
+    return SP_ECUDA;
+}
+
+// A gulp whose search candidates are on the host: without an attached stage
+// it is finished; else its candidates are sifted, and with a classifier the
+// kept peaks join the open classification job.  Slot si was freed already
+// unless a classifier is attached; then it is held until the gulp's job has
+// finished (or freed here when the gulp has no peak to score).
+int finish_search(sp_stream *s, Result &&r, int si) {
+    if (!s->attached) {
+        s->results.push_back(std::move(r));
+        return SP_OK;
+    }
+    const sp_plan *p = s->plan;
+    int64_t nk = 0;
+    int rc = sp_sift(r.cands.empty() ? nullptr : r.cands.data(), (int64_t)r.cands.size(), p->dms.data(), p->ndm,
+                     s->widths, s->nw, p->tsamp, &s->sift, s->sift_buf.data(), s->kept_cap, &nk, nullptr);
+    if (rc == SP_EOVERFLOW) {
+        r.info.status = SP_EOVERFLOW;
+        rc = SP_OK;
+    }
+    const int32_t n = rc ? 0 : (int32_t)std::min<int64_t>(nk, s->kept_cap);
+    if (rc) r.info.status = rc;
+    r.info.kept = rc ? 0 : nk;
+    r.kept.assign(s->sift_buf.begin(), s->sift_buf.begin() + n);
+    if (!s->clf || n == 0) {
+        r.prob.assign((size_t)n, -1.0f);
+        r.info.accepted = s->clf ? 0 : n;
+        s->results.push_back(std::move(r));
+        if (s->clf) s->free_slots.push_back(si);  // held only for the classifier
+        return SP_OK;
+    }
+    if (s->open_job >= 0 && s->recs[s->open_job].total + n > kClsCap) {
+        rc = dispatch_job(s);
+        if (rc) return rc;
+    }
+    if (s->open_job < 0) {  // a record is free: every job holds at least one slot
+        s->open_job = s->free_recs.back();
+        s->free_recs.pop_back();
+    }
+    JobRec &j = s->recs[s->open_job];
+    std::memcpy(j.h_kept + j.total, r.kept.data(), (size_t)n * sizeof(sp_cand));
+    j.first.push_back(j.total);
+    j.total += n;
+    j.slots.push_back(si);
+    j.rs.push_back(std::move(r));
+    return SP_OK;
+}
+
+// Collects finished classifications and launches, then starts new launches
+// while possible.
 int progress(sp_stream *s) {
+    while (!s->jobs.empty()) {
+        const int id = s->jobs.front();
+        JobRec &j = s->recs[id];
+        const cudaError_t q = cudaEventQuery(j.done);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) return SP_ECUDA;
+        for (long spins = 0; !j.finished.load(std::memory_order_acquire) && spins < (1L << 26); ++spins) {
+        }
+        const double t_done = j.finished.load(std::memory_order_acquire) ? j.t_done : now_s();
+        for (size_t g = 0; g < j.rs.size(); ++g) {
+            Result &r = j.rs[g];
+            r.prob.assign(j.h_prob + j.first[g], j.h_prob + j.first[g] + r.kept.size());
+            r.info.accepted = 0;
+            for (float v : r.prob) r.info.accepted += v >= 0.5f;
+            r.info.t_done = t_done;
+            s->results.push_back(std::move(r));
+            s->free_slots.push_back(j.slots[g]);
+        }
+        j.rs.clear();
+        j.slots.clear();
+        j.first.clear();
+        j.total = 0;
+        s->free_recs.push_back(id);
+        s->jobs.pop_front();
+    }
     for (int li = 0; li < s->nstreams; ++li) {
         Launch &L = s->launches[li];
         if (!L.busy) continue;
@@ -298,29 +519,46 @@ int progress(sp_stream *s) {
         for (long spins = 0; !L.finished.load(std::memory_order_acquire) && spins < (1L << 26); ++spins) {
         }
         if (!L.finished.load(std::memory_order_acquire)) L.t_done = now_s();
+        L.busy = false;
+        // The candidates are on the host now: unless the classifier will read
+        // the staged window, the slot is free for the next batch at once.
+        const bool hold = s->attached && s->clf;
         for (size_t i = 0; i < L.gulps.size(); ++i) {
             const Slot &sl = s->slots[L.slots[i]];
-            Result r;
-            r.info.beam = L.gulps[i].beam;
-            r.info.seq = L.gulps[i].seq;
-            r.info.t0 = L.gulps[i].seq * s->gulp;
-            r.info.count = *sl.h_count;
-            r.info.status = *sl.h_count > s->cap ? SP_EOVERFLOW : SP_OK;
-            r.info.t_push = L.gulps[i].t_push;
-            r.info.t_done = L.t_done;
-            r.cands.assign(sl.h_cands, sl.h_cands + std::min(*sl.h_count, s->cap));
-            s->results.push_back(std::move(r));
-            s->free_slots.push_back(L.slots[i]);
+            Searched g;
+            std::memset(&g.r.info, 0, sizeof g.r.info);
+            g.r.info.beam = L.gulps[i].beam;
+            g.r.info.seq = L.gulps[i].seq;
+            g.r.info.t0 = L.gulps[i].seq * s->gulp;
+            g.r.info.count = *sl.h_count;
+            g.r.info.status = *sl.h_count > s->cap ? SP_EOVERFLOW : SP_OK;
+            g.r.info.t_push = L.gulps[i].t_push;
+            g.r.info.t_done = L.t_done;
+            g.r.info.t_search = L.t_done;
+            g.r.cands.assign(sl.h_cands, sl.h_cands + std::min(*sl.h_count, s->cap));
+            g.slot = L.slots[i];
+            if (!hold) s->free_slots.push_back(g.slot);
+            s->searched.push_back(std::move(g));
         }
-        L.busy = false;
     }
+    // New batches first, then the host-side sifting and the classification
+    // of the searched gulps, so that the GPU is never waiting for the sifter.
     for (int li = 0; li < s->nstreams; ++li) {
         if (s->pending.empty() || s->free_slots.empty()) break;
         if (s->launches[li].busy) continue;
         const int rc = launch_batch(s, li);
         if (rc) return rc;
     }
-    return SP_OK;
+    int rc = SP_OK;
+    while (!s->searched.empty()) {
+        Searched &g = s->searched.front();
+        const int e = finish_search(s, std::move(g.r), g.slot);
+        if (e && !rc) rc = e;
+        s->searched.pop_front();
+    }
+    const int e = dispatch_job(s);
+    if (e && !rc) rc = e;
+    return rc;
 }
 
 }  // namespace
@@ -362,14 +600,16 @@ extern "C" int sp_stream_create(const sp_plan *plan, int32_t nbeams, int64_t gul
     s->has_history.assign(nbeams, 0);
     s->staged_ev.assign(nbeams, nullptr);
     s->staged_ev_used.assign(nbeams, 0);
-    // Memory: the rings first, then as many slots as the budget allows (at
-    // most one batch per launch stream is useful).
+    // Memory: the rings first, then as many slots as the budget allows: one
+    // batch per launch stream, plus one batch more so that a batch can be
+    // admitted while the slots of an earlier one are still held by its
+    // classification (sp_stream_attach).
     const int64_t tables = s->nstreams * (align256((int64_t)max_batch * sizeof(BatchBeamDev)) +
                                           align256((int64_t)(max_batch + 1) * 8) + 256);
     const int64_t rings = (int64_t)nbeams * s->ring_bytes;
     const int64_t per_slot = slot_bytes(s);
     const int64_t nslots = std::min<int64_t>((hbm_budget_bytes - rings - tables) / per_slot,
-                                             (int64_t)max_batch * s->nstreams);
+                                             (int64_t)max_batch * (s->nstreams + 1));
     if (nslots < 1) rc = SP_ENOMEM;
     if (!rc) rc = alloc_dev((void **)&s->d_rings, rings, &s->device_bytes);
     if (!rc && cudaMemset(s->d_rings, 0, (size_t)rings) != cudaSuccess) rc = SP_ECUDA;
@@ -393,7 +633,16 @@ extern "C" int sp_stream_create(const sp_plan *plan, int32_t nbeams, int64_t gul
         if (!rc) rc = alloc_dev((void **)&L.d_begin, (int64_t)(max_batch + 1) * 8, &s->device_bytes);
         if (!rc) rc = alloc_dev((void **)&L.d_counter, 8, &s->device_bytes);
         if (!rc && (cudaStreamCreateWithFlags(&s->streams[li], cudaStreamNonBlocking) != cudaSuccess ||
-                    cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess)) {
+                    cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&L.dedispersed, cudaEventDisableTiming) != cudaSuccess)) {
+            cudaGetLastError();
+            rc = SP_ECUDA;
+        }
+    }
+    if (!rc && !(flags & SP_STREAM_ONE_STREAM)) {
+        int prio_lo = 0, prio_hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&s->search_stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
             cudaGetLastError();
             rc = SP_ECUDA;
         }
@@ -426,6 +675,8 @@ extern "C" int sp_stream_destroy(sp_stream *s) {
     if (!s) return SP_EINVAL;
     for (int li = 0; li < s->nstreams; ++li)
         if (s->streams[li]) cudaStreamSynchronize(s->streams[li]);
+    if (s->search_stream) cudaStreamSynchronize(s->search_stream);
+    if (s->cls_stream) cudaStreamSynchronize(s->cls_stream);
     stream_free(s);
     delete s;
     return SP_OK;
@@ -463,23 +714,35 @@ extern "C" int sp_stream_push(sp_stream *s, int32_t beam, const uint8_t *h_gulp,
     g.h = h_gulp;
     g.t_push = now_s();
     s->pending.push_back(g);
+    s->pushed = true;
     if (seq) *seq = g.seq;
     return progress(s);
 }
 
-extern "C" int sp_stream_poll(sp_stream *s, int32_t wait, sp_gulp_result *out, sp_cand *cands, int32_t max_results,
-                              int32_t *n_results) {
+namespace {
+
+int poll_impl(sp_stream *s, int32_t wait, sp_gulp_result *out, sp_cand *cands, sp_cand *kept, float *prob,
+              int32_t max_results, int32_t *n_results) {
     if (!s || !n_results || max_results < 0 || (max_results > 0 && !out)) return SP_EINVAL;
     *n_results = 0;
     int rc = progress(s);
     if (rc) return rc;
-    if (wait && s->results.empty()) {
-        // Wait for the launch that finishes first (the older one).
-        for (int li = 0; li < s->nstreams; ++li)
-            if (s->launches[li].busy) {
-                if (cudaEventSynchronize(s->launches[li].done) != cudaSuccess) return SP_ECUDA;
-                break;
-            }
+    // Wait for the oldest classification, else the older launch, until a
+    // result is ready or nothing is in flight (each wait ends with the work
+    // it waits for).
+    while (wait && s->results.empty()) {
+        cudaEvent_t e = nullptr;
+        if (!s->jobs.empty()) {
+            e = s->recs[s->jobs.front()].done;
+        } else {
+            const Launch *oldest = nullptr;
+            for (int li = 0; li < s->nstreams; ++li)
+                if (s->launches[li].busy && (!oldest || s->launches[li].order < oldest->order))
+                    oldest = &s->launches[li];
+            if (oldest) e = oldest->done;
+        }
+        if (!e) break;
+        if (cudaEventSynchronize(e) != cudaSuccess) return SP_ECUDA;
         rc = progress(s);
         if (rc) return rc;
     }
@@ -489,6 +752,10 @@ extern "C" int sp_stream_poll(sp_stream *s, int32_t wait, sp_gulp_result *out, s
         out[n] = r.info;
         if (cands && !r.cands.empty())
             std::memcpy(cands + (int64_t)n * s->cap, r.cands.data(), r.cands.size() * sizeof(sp_cand));
+        if (kept && !r.kept.empty())
+            std::memcpy(kept + (int64_t)n * s->kept_cap, r.kept.data(), r.kept.size() * sizeof(sp_cand));
+        if (prob && !r.prob.empty())
+            std::memcpy(prob + (int64_t)n * s->kept_cap, r.prob.data(), r.prob.size() * sizeof(float));
         s->results.pop_front();
         ++n;
     }
@@ -496,13 +763,84 @@ extern "C" int sp_stream_poll(sp_stream *s, int32_t wait, sp_gulp_result *out, s
     return SP_OK;
 }
 
+}  // namespace
+
+extern "C" int sp_stream_poll(sp_stream *s, int32_t wait, sp_gulp_result *out, sp_cand *cands, int32_t max_results,
+                              int32_t *n_results) {
+    return poll_impl(s, wait, out, cands, nullptr, nullptr, max_results, n_results);
+}
+
+extern "C" int sp_stream_poll_sifted(sp_stream *s, int32_t wait, sp_gulp_result *out, sp_cand *cands, sp_cand *kept,
+                                     float *prob, int32_t max_results, int32_t *n_results) {
+    if (s && !s->attached) return SP_EINVAL;
+    return poll_impl(s, wait, out, cands, kept, prob, max_results, n_results);
+}
+
 extern "C" int sp_stream_pending(const sp_stream *s, int64_t *queued, int64_t *in_flight, int64_t *ready) {
     if (!s) return SP_EINVAL;
-    int64_t f = 0;
+    int64_t f = (int64_t)s->jobs.size();
     for (int li = 0; li < s->nstreams; ++li)
         if (s->launches[li].busy) f += (int64_t)s->launches[li].gulps.size();
     if (queued) *queued = (int64_t)s->pending.size();
     if (in_flight) *in_flight = f;
     if (ready) *ready = (int64_t)s->results.size();
+    return SP_OK;
+}
+
+extern "C" int sp_stream_attach(sp_stream *s, const sp_sift_params *params, sp_cnn *clf, int32_t t_in,
+                                int32_t kept_cap) {
+    if (!s || !params || s->attached || s->pushed || kept_cap < 1 || kept_cap > kClsCap) return SP_EINVAL;
+    const sp_plan *p = s->plan;
+    if (clf && (p->nchan % 256 || t_in < 256 || t_in > 4096 || (t_in & 1) || cnn_device(clf) != s->device))
+        return SP_EINVAL;
+    int64_t dummy = 0;  // the sifter's own argument checks, on no candidates
+    int rc = sp_sift(nullptr, 0, p->dms.data(), p->ndm, s->widths, s->nw, p->tsamp, params, nullptr, 0, &dummy, nullptr);
+    if (rc) return rc;
+    if (!on_plan_device(p)) return SP_EINVAL;
+    s->sift_buf.assign((size_t)kept_cap, sp_cand{});
+    if (clf) {
+        const int64_t nimg = (int64_t)kClsCap * 256 * 256;
+        s->work_bytes = sp_cnn_features_workspace_bytes(kClsCap);
+        rc = alloc_dev((void **)&s->d_kept, (int64_t)kClsCap * (int64_t)sizeof(sp_cand), &s->device_bytes);
+        if (!rc) rc = alloc_dev((void **)&s->d_sub, (int64_t)kClsCap * 256 * t_in * 4, &s->device_bytes);
+        if (!rc) rc = alloc_dev(&s->d_ft, nimg * 2, &s->device_bytes);
+        if (!rc) rc = alloc_dev(&s->d_img, nimg * 2, &s->device_bytes);
+        if (!rc) rc = alloc_dev(&s->d_work, s->work_bytes, &s->device_bytes);
+        if (!rc) rc = alloc_dev((void **)&s->d_shift, 256 * 256 * 4, &s->device_bytes);
+        if (!rc) rc = alloc_dev((void **)&s->d_prob, (int64_t)kClsCap * 4, &s->device_bytes);
+        if (!rc) {
+            s->recs.reset(new (std::nothrow) JobRec[s->slots.size()]);
+            if (!s->recs) rc = SP_ENOMEM;
+        }
+        for (size_t i = 0; i < s->slots.size() && !rc; ++i) {
+            JobRec &j = s->recs[i];
+            rc = alloc_host((void **)&j.h_kept, (int64_t)kClsCap * (int64_t)sizeof(sp_cand));
+            if (!rc) rc = alloc_host((void **)&j.h_prob, (int64_t)kClsCap * 4);
+            if (!rc && cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                rc = SP_ECUDA;
+            }
+            s->free_recs.push_back((int)i);
+        }
+        std::vector<int32_t> shift((size_t)256 * 256);
+        if (!rc) rc = sp_dmt_shifts(p->freqs.data(), p->nchan, 256, (t_in - 256) / 2, shift.data());
+        if (!rc && cudaMemcpy(s->d_shift, shift.data(), shift.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = SP_ECUDA;
+        // The classifier's kernels are few and short: the highest priority lets
+        // them take SMs as soon as any free up instead of queueing behind the
+        // CTAs of the next dedispersion batch.
+        int prio_lo = 0, prio_hi = 0;
+        if (!rc && (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
+                    cudaStreamCreateWithPriority(&s->cls_stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess)) {
+            cudaGetLastError();
+            rc = SP_ECUDA;
+        }
+        if (rc) return rc;  // what was allocated is freed by sp_stream_destroy
+    }
+    s->sift = *params;
+    s->clf = clf;
+    s->t_in = t_in;
+    s->kept_cap = kept_cap;
+    s->attached = true;
     return SP_OK;
 }

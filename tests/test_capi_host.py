@@ -139,7 +139,9 @@ def test_stream_argument_checks(lib):
     for fn, args in [("sp_stream_destroy", [None]), ("sp_stream_info", [None, None, None, None]),
                      ("sp_stream_history", [None, 0, None]), ("sp_stream_push", [None, 0, None, None]),
                      ("sp_stream_poll", [None, 0, None, None, 0, None]),
-                     ("sp_stream_pending", [None, None, None, None])]:
+                     ("sp_stream_pending", [None, None, None, None]),
+                     ("sp_stream_attach", [None, None, None, 512, 64]),
+                     ("sp_stream_poll_sifted", [None, 0, None, None, None, None, 0, None])]:
         assert getattr(lib, fn)(*args) == sp.SP_EINVAL, fn
     t0 = lib.sp_stream_now()
     t1 = lib.sp_stream_now()

@@ -158,3 +158,70 @@ def test_stream_full_band_gulps():
     _check_oracle(res, beams, f, dms, gulp, dmax)
     assert plan.status() == 0
     s.close()
+
+
+@pytest.mark.parametrize("with_classifier", [False, True])
+def test_stream_sift_and_classify_in_the_stream(with_classifier):
+    """A sifter (and classifier) attached to the stream (Sec. 3.2 per
+    searched block): each gulp's kept peaks equal sp_sift of the gulp's own
+    candidates, and each probability equals the standalone chain -- stage
+    the window, sp_cnn_extract, sp_cnn_features, sp_cnn_forward -- on the
+    same window; the forward batches of 4 inside the stream split 8 peaks."""
+    nchan, gulp, ngulps, nbeams = 256, 1500, 5, 3
+    dms = np.arange(0, 120.0, 1.0)
+    f, dmax, data = _streams(nchan, dms, gulp, ngulps, nbeams, 57)
+    plan = sp.Plan(f, synth.TSAMP, dms)
+    beams = dict(enumerate(data))
+    clf = sp.Classifier(max_batch=4, seed=3) if with_classifier else None
+    s = sp.Stream(plan, nbeams, gulp, WIDTHS, 6.0, 8192, 4096, 1 << 32, max_batch=3)
+    s.attach(clf, t_in=512, kept_cap=8, min_points=2, snr_min=8.0)
+    with pytest.raises(sp.SpotlightError):
+        s.attach(clf)  # once only
+    for b, (_, hist, _, _) in beams.items():
+        s.history(b, hist)
+    res = {}
+    for k in range(ngulps):
+        for b in range(nbeams):
+            s.push(b, beams[b][2][k])
+            for r, c, kept, prob in s.poll_sifted(with_cands=True):
+                res[(r.beam, r.seq)] = (r, c, kept, prob)
+    for r, c, kept, prob in s.drain(with_cands=True, sifted=True):
+        res[(r.beam, r.seq)] = (r, c, kept, prob)
+    assert len(res) == nbeams * ngulps
+    with pytest.raises(sp.SpotlightError):
+        s.attach(clf)  # not after a push
+    t_in, classified = 512, 0
+    shift = torch.from_numpy(sp.dmt_shifts(f, 256, (t_in - 256) // 2)).cuda()
+    for (b, k), (r, c, kept, prob) in sorted(res.items()):
+        assert r.status == sp.SP_OK and r.count == c.size
+        assert r.t_done >= r.t_search >= r.t_push > 0
+        want = sp.sift(c, dms, WIDTHS, synth.TSAMP, min_points=2, snr_min=8.0)
+        assert r.kept == want.size
+        assert np.array_equal(kept, want[:8])
+        if not with_classifier:
+            assert np.all(prob == -1.0) and r.accepted == kept.size
+            continue
+        if kept.size == 0:
+            assert r.accepted == 0
+            continue
+        classified += 1
+        x = beams[b][0]
+        win = torch.from_numpy(np.ascontiguousarray(x[k * gulp:k * gulp + gulp + dmax])).cuda()
+        staged = sp.staged_buffer(nchan, win.shape[0])
+        sp.stage_input(win, staged)
+        d_c = torch.from_numpy(np.ascontiguousarray(kept).view(np.int32).reshape(-1, 4)).cuda()
+        sub = sp.cnn_extract(plan, staged, win.shape[0], d_c, WIDTHS, t_in=t_in)
+        n = kept.size
+        ft = torch.empty((n, 256, 256), dtype=torch.bfloat16, device="cuda")
+        img = torch.empty_like(ft)
+        sp.cnn_features(sub, shift, ft, img)
+        p = torch.empty(n, dtype=torch.float32, device="cuda")
+        for i in range(0, n, 4):
+            j = min(n, i + 4)
+            clf.forward(ft[i:j].contiguous(), img[i:j].contiguous(), p[i:j])
+        p = p.cpu().numpy()
+        assert np.array_equal(prob, p), (b, k, prob, p)
+        assert r.accepted == int((p >= 0.5).sum())
+    if with_classifier:
+        assert classified >= nbeams  # every beam's bursts reach the classifier
+    s.close()

@@ -9,14 +9,15 @@
 //                       cp.async double buffering, optional split-K; the
 //                       epilogue adds a bias and applies ReLU (bf16 out),
 //                       stores fp32, or adds fp32 atomically.
-//   im2col_kernel       3x3 / stride / pad-1 patches of an NHWC bf16 tensor
-//                       as GEMM rows, k = (ky*3 + kx)*C + c, zero padded.
+//   im2col_*_kernel     3x3 / stride / pad-1 patches of an NHWC bf16 tensor
+//                       as GEMM rows, k = (ky*3 + kx)*C + c, zero padded
+//                       (16-byte copies for C % 8 == 0 and for C == 1).
 //   col2im_relu_kernel  the adjoint of im2col (a gather, no atomics) fused
 //                       with the ReLU derivative of the layer below.
 //   transpose_kernel    bf16 [R][C] -> [C][R] (operands of the backward GEMMs).
-//   features_kernel     frequency-time and DM-time images of a subband
-//                       dynamic spectrum, each normalised to zero mean and
-//                       unit variance, as bf16.
+//   features_raw_kernel frequency-time and DM-time images of a subband
+//   normalise_kernel    dynamic spectrum, then each normalised to zero mean
+//                       and unit variance, as bf16.
 //   plus average pooling, the linear heads, the fused loss and Adam.
 #include <cuda_bf16.h>
 
@@ -160,6 +161,50 @@ __global__ void __launch_bounds__(256) gemm_nt_kernel(const __nv_bfloat16 *__res
 }
 
 // cols[p][k] for p = (n, ho, wo), k = (ky*3 + kx)*C + c (k < 9C; zero up to Kp).
+// Channels a multiple of 8: one thread per (patch row p, chunk j of 8
+// columns).  Chunk j is one tap (ky, kx) = divmod(8j / C, 3) and channels
+// 8j % C .. + 7 of one pixel: a single 16-byte copy (zero outside the image
+// and past 9C).  32-bit index arithmetic (the launcher checks the sizes).
+__global__ void im2col_vec_kernel(const __nv_bfloat16 *__restrict__ x, int H, int W, int C, int stride, int Ho,
+                                  int Wo, uint32_t chunks, uint32_t total, __nv_bfloat16 *__restrict__ cols) {
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const uint32_t p = idx / chunks, j = idx - p * chunks;
+        const uint32_t k0 = j * 8u, tap = k0 / (uint32_t)C, c0 = k0 - tap * (uint32_t)C;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (tap < 9u) {
+            const uint32_t t = p / (uint32_t)Wo, wo = p - t * (uint32_t)Wo;
+            const uint32_t n = t / (uint32_t)Ho, ho = t - n * (uint32_t)Ho;
+            const int h = (int)ho * stride - 1 + (int)(tap / 3u), w = (int)wo * stride - 1 + (int)(tap % 3u);
+            if (h >= 0 && h < H && w >= 0 && w < W)
+                v = *reinterpret_cast<const uint4 *>(x + ((size_t)(n * (uint32_t)H + (uint32_t)h) * W + w) * C + c0);
+        }
+        reinterpret_cast<uint4 *>(cols)[idx] = v;
+    }
+}
+
+// One channel (the first layer): one thread per patch row, its nine taps
+// gathered and the row of Kp columns written as 16-byte stores.
+__global__ void im2col_c1_kernel(const __nv_bfloat16 *__restrict__ x, int H, int W, int stride, int Ho, int Wo,
+                                 uint32_t kp_chunks, uint32_t P, __nv_bfloat16 *__restrict__ cols) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const uint32_t t = p / (uint32_t)Wo, wo = p - t * (uint32_t)Wo;
+        const uint32_t n = t / (uint32_t)Ho, ho = t - n * (uint32_t)Ho;
+        __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = __float2bfloat16(0.f);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int h = (int)ho * stride - 1 + k / 3, w = (int)wo * stride - 1 + k % 3;
+            if (h >= 0 && h < H && w >= 0 && w < W) v[k] = x[((size_t)n * H + h) * W + w];
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(cols) + (size_t)p * kp_chunks;
+        dst[0] = *reinterpret_cast<const uint4 *>(&v[0]);
+        dst[1] = *reinterpret_cast<const uint4 *>(&v[8]);
+        for (uint32_t j = 2; j < kp_chunks; ++j) dst[j] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Any channel count (reference form, one element per thread).
 __global__ void im2col_kernel(const __nv_bfloat16 *__restrict__ x, int Nb, int H, int W, int C, int stride, int Ho,
                               int Wo, int Kp, __nv_bfloat16 *__restrict__ cols) {
     const int64_t total = (int64_t)Nb * Ho * Wo * Kp;
@@ -349,19 +394,50 @@ __global__ void to_bf16_kernel(const float *__restrict__ a, int64_t n, __nv_bflo
 // u0 = (T_in - 256) / 2.  Each image is then set to zero mean and unit
 // variance (computed in fp32 over its 65536 values) and stored as bf16.
 // One CTA (256 threads) per (candidate, image row); a second pass normalises.
-__global__ void features_raw_kernel(const float *__restrict__ sub, int S, int T_in, const int32_t *__restrict__ shift,
-                                    float *__restrict__ ft_raw, float *__restrict__ dmt_raw) {
-    const int b = blockIdx.y, row = blockIdx.x, u = threadIdx.x;
+// Raw images of candidate b: ft_raw[b][s][u] = sub[b][s][u0 + u] and
+// dmt_raw[b][j][u] = sum over subbands k (in order) of sub[b][k][u0 + u +
+// shift[j][k]] (bins outside the spectrum count 0), u0 = (T_in - 256) / 2.
+// One CTA per (block of kFeatRows rows j, candidate), one thread per bin u:
+// subband k's whole row of T_in bins is staged in shared memory (double
+// buffered) and serves the CTA's kFeatRows shifted sums at once, with the
+// block's shift table transposed beside it.  (A third buffer with the next
+// row prefetched into registers ran at half the speed: fewer CTAs per SM.)
+constexpr int kFeatRows = 32;
+__global__ void __launch_bounds__(kImg) features_raw_kernel(const float *__restrict__ sub, int T_in,
+                                                            const int32_t *__restrict__ shift,
+                                                            float *__restrict__ ft_raw, float *__restrict__ dmt_raw) {
+    extern __shared__ __align__(16) float fsm[];
+    float *rows = fsm;                                          // [2][T_in]
+    int32_t *sh = reinterpret_cast<int32_t *>(fsm + 2 * T_in);  // [kImg subbands][kFeatRows]
+    const int b = blockIdx.y, j0 = blockIdx.x * kFeatRows, u = threadIdx.x;
     const int u0 = (T_in - kImg) / 2;
-    const float *sb = sub + (int64_t)b * S * T_in;
-    if (row < S) ft_raw[((int64_t)b * kImg + row) * kImg + u] = sb[(int64_t)row * T_in + u0 + u];
-    float s = 0.f;
-    const int32_t *sh = shift + (int64_t)row * S;
-    for (int k = 0; k < S; ++k) {
-        const int t = u0 + u + sh[k];
-        if (t >= 0 && t < T_in) s += sb[(int64_t)k * T_in + t];
+    const float *sb = sub + (size_t)b * kImg * T_in;
+    for (int r = 0; r < kFeatRows; ++r)
+        ft_raw[((size_t)b * kImg + j0 + r) * kImg + u] = sb[(size_t)(j0 + r) * T_in + u0 + u];
+    for (int i = threadIdx.x; i < kImg * kFeatRows; i += blockDim.x) {
+        const int r = i / kImg, k = i - r * kImg;
+        sh[k * kFeatRows + r] = shift[(size_t)(j0 + r) * kImg + k];
     }
-    dmt_raw[((int64_t)b * kImg + row) * kImg + u] = s;
+    for (int i = threadIdx.x; i < T_in; i += blockDim.x) rows[i] = sb[i];
+    __syncthreads();
+    float acc[kFeatRows];
+#pragma unroll
+    for (int r = 0; r < kFeatRows; ++r) acc[r] = 0.f;
+    for (int k = 0; k < kImg; ++k) {
+        const float *cur = rows + (k & 1) * T_in;
+        float *nxt = rows + ((k + 1) & 1) * T_in;  // read last in step k - 1, before its barrier
+        if (k + 1 < kImg)
+            for (int i = threadIdx.x; i < T_in; i += blockDim.x) nxt[i] = sb[(size_t)(k + 1) * T_in + i];
+        const int32_t *shk = sh + k * kFeatRows;
+#pragma unroll
+        for (int r = 0; r < kFeatRows; ++r) {
+            const int t = u0 + u + shk[r];
+            if ((unsigned)t < (unsigned)T_in) acc[r] += cur[t];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < kFeatRows; ++r) dmt_raw[((size_t)b * kImg + j0 + r) * kImg + u] = acc[r];
 }
 
 __global__ void normalise_kernel(const float *__restrict__ raw, __nv_bfloat16 *__restrict__ out) {
@@ -446,7 +522,18 @@ int cnn_gemm(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *
 
 int cnn_im2col(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho, int Wo, int Kp,
                __nv_bfloat16 *cols, cudaStream_t st) {
-    im2col_kernel<<<grid_for((int64_t)Nb * Ho * Wo * Kp), 256, 0, st>>>(x, Nb, H, W, C, stride, Ho, Wo, Kp, cols);
+    const int64_t P = (int64_t)Nb * Ho * Wo;
+    const bool small = P * Kp < (int64_t)1 << 31 && (int64_t)Nb * H * W * C < (int64_t)1 << 31;
+    const bool aligned = (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(cols) & 15) == 0;
+    if (small && aligned && Kp % 8 == 0 && C % 8 == 0) {
+        const int64_t total = P * (Kp / 8);
+        im2col_vec_kernel<<<grid_for(total), 256, 0, st>>>(x, H, W, C, stride, Ho, Wo, (uint32_t)(Kp / 8),
+                                                           (uint32_t)total, cols);
+    } else if (small && aligned && Kp % 8 == 0 && Kp >= 16 && C == 1) {
+        im2col_c1_kernel<<<grid_for(P), 256, 0, st>>>(x, H, W, stride, Ho, Wo, (uint32_t)(Kp / 8), (uint32_t)P, cols);
+    } else {
+        im2col_kernel<<<grid_for(P * Kp), 256, 0, st>>>(x, Nb, H, W, C, stride, Ho, Wo, Kp, cols);
+    }
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
@@ -519,8 +606,13 @@ int cnn_extract(const uint8_t *xt, int64_t pitch, int64_t n_in, int32_t nchan, c
 
 int cnn_features(const float *sub, int Nb, int S, int T_in, const int32_t *shift, float *ft_raw, float *dmt_raw,
                  __nv_bfloat16 *ft, __nv_bfloat16 *dmt, cudaStream_t st) {
-    if (S != kImg || T_in < kImg) return SP_EINVAL;
-    features_raw_kernel<<<dim3(kImg, Nb), kImg, 0, st>>>(sub, S, T_in, shift, ft_raw, dmt_raw);
+    if (S != kImg || T_in < kImg || T_in > 4096) return SP_EINVAL;
+    const size_t smem = (size_t)2 * T_in * 4 + (size_t)kImg * kFeatRows * 4;  // <= 32 KB + 32 KB
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(features_raw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return SP_ECUDA;
+    features_raw_kernel<<<dim3(kImg / kFeatRows, Nb), kImg, smem, st>>>(sub, T_in, shift, ft_raw, dmt_raw);
     if (cudaGetLastError() != cudaSuccess) return SP_ECUDA;
     normalise_kernel<<<Nb, 256, 0, st>>>(ft_raw, ft);
     normalise_kernel<<<Nb, 256, 0, st>>>(dmt_raw, dmt);

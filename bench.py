@@ -290,10 +290,12 @@ def run_ours(args):
     clocks.start()
     barrier(world)
     torch.cuda.synchronize(dev)
+    lc0 = sp.launch_count()
     t_start.record(stream)
     for k in range(args.steps):
         step(evs[k])
     t_end.record(stream)
+    launches = sp.launch_count() - lc0
     torch.cuda.synchronize(dev)
     barrier(world)
     clk = clocks.stop()
@@ -346,7 +348,8 @@ def run_ours(args):
                      "kernel": "dedisperse_kernel",
                      "peak_basis": f"{nsm} SMs x {lanes:.1f} measured 32-bit add lanes/SM/clk x "
                                    f"{MAX_SM_MHZ:.0f} MHz"},
-        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+        "kernels_per_step": KERNELS_PER_STEP,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -402,11 +405,13 @@ def run_batched(args):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         barrier(world)
         torch.cuda.synchronize(dev)
+        lc0 = sp.launch_count()
         ev[0].record(stream)
         for k in range(steps):
             batch.launch(stream)
             ev[k + 1].record(stream)
         torch.cuda.synchronize(dev)
+        timed_graph.launches = sp.launch_count() - lc0
         barrier(world)
         return reduce_max(ev[0].elapsed_time(ev[-1]), world, dev) / steps
 
@@ -424,6 +429,7 @@ def run_batched(args):
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     ms_step = timed_graph(main_mode, args.steps, args.warmup)
+    launches = timed_graph.launches
     clk = clocks.stop()
     counts = [batch.count(b, stream) for b in range(bw.nbeams)]
     value = world * data_s / (ms_step / 1e3)
@@ -475,7 +481,7 @@ def run_batched(args):
                      "peak_basis": f"{nsm} SMs x {lanes:.1f} measured 32-bit add lanes/SM/clk x "
                                    f"{MAX_SM_MHZ:.0f} MHz"},
         "e2e": None, "cpu_baseline": cpu, "clocks": clk,
-        "gpu_launches": (4 * bw.nbeams + ngroups) * args.steps,  # per beam: staging, statistics, boxcar, 64-bit pass; per group: dedispersion
+        "gpu_launches": launches,  # per beam: staging, statistics, boxcar, 64-bit pass; per group: dedispersion
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -576,13 +582,14 @@ def run_stream(args):
         poll(wait=True)  # warm-up round
         tally[:] = [0, 0, 0]
         barrier(world)
+        lc0 = sp.launch_count()
         t0 = time.perf_counter()
         for _ in range(rounds):
             one_round()
         poll(wait=True)
         dt = reduce_max(time.perf_counter() - t0, world, dev)
         info = {"slots": s.slots, "device_bytes": s.device_bytes, "candidates": tally[0], "kept": tally[1],
-                "accepted": tally[2]}
+                "accepted": tally[2], "launches": sp.launch_count() - lc0}
         s.close()
         return rounds * nbeams / dt, dt, info
 
@@ -660,7 +667,7 @@ def run_stream(args):
                 "d2h_bytes_per_step": 8 + 16 * cap + 4 * kept_cap,
                 "api": "sp_stream_push / sp_stream_poll_sifted from pinned host gulps"},
         "cpu_baseline": None, "clocks": clk,
-        "gpu_launches": None,
+        "gpu_launches": info_b["launches"],
     }
     lanes, nsm = sp.probe_iadd3_rate()
     peak = nsm * lanes * MAX_SM_MHZ * 1e6 / 1e12
@@ -741,12 +748,14 @@ def run_classifier(args):
         clf.forward(ft, dmt, prob)
     torch.cuda.synchronize(dev)
     reps = max(args.steps, 1) * 10
+    lc0 = sp.launch_count()
     e0.record(stream)
     for _ in range(reps):
         sp.cnn_features(big, shift, ft, dmt, work)
         clf.forward(ft, dmt, prob)
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    launches = sp.launch_count() - lc0
     infer_ms = e0.elapsed_time(e1) / reps
     clk = clocks.stop()
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1900.0)
@@ -767,7 +776,7 @@ def run_classifier(args):
                      "kernel": "inference step (features + im2col + gemm_nt_kernel + pooling/head), algorithmic "
                                "convolution FLOPs over the step time",
                      "peak_basis": "measured bf16 GEMM burst (MEASURED_PEAKS.json)"},
-        "e2e": None, "cpu_baseline": None, "clocks": clk, "gpu_launches": None,
+        "e2e": None, "cpu_baseline": None, "clocks": clk, "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
 

@@ -63,6 +63,12 @@ typedef struct {
 
 const char *sp_strerror(int code);
 
+/* Kernel launches the library has issued in this process, for measurement
+ * (no counterpart in the paper): every kernel a call launches counts once;
+ * kernels recorded into a CUDA graph (sp_batch_capture) count once per
+ * replay (sp_batch_launch), not at capture.  Never fails. */
+uint64_t sp_launch_count(void);
+
 /* ------------------------------------------------------------------ plan --
  * Dedispersion plan (Sec. 3.1.1).  For trial DM d and channel c the delay is
  *   delay[d][c] = floor(x + 0.5),

@@ -20,6 +20,7 @@ Names mirror the C entry points:
 * ``sift``                       sp_sift (DBSCAN clustering + thresholds, host)
 * ``inject_quantised``           sp_inject_quantised (Appendix B injection)
 * ``Classifier``, ``cnn_features``, ``dmt_shifts``  sp_cnn_* (two-image CNN)
+* ``launch_count``               sp_launch_count (kernels issued, for measurement)
 """
 from __future__ import annotations
 
@@ -98,6 +99,7 @@ SIGNATURES = {
     "sp_stream_pending": (ctypes.c_int, [P, P, P, P]),
     "sp_stream_now": (F64, []),
     "sp_stream_attach": (ctypes.c_int, [P, P, P, I32, I32]),
+    "sp_launch_count": (ctypes.c_uint64, []),
     "sp_stream_poll_sifted": (ctypes.c_int, [P, I32, P, P, P, P, I32, P]),
     "sp_sift": (ctypes.c_int, [P, I64, P, I32, P, I32, F64, P, P, I64, P, P]),
     "sp_inject_quantised": (ctypes.c_int, [P, P, I64, I32, F64, F64, F64, P]),
@@ -530,6 +532,12 @@ class GulpResult(ctypes.Structure):
                 ("t0", ctypes.c_int64), ("count", ctypes.c_int64), ("t_push", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("t_search", ctypes.c_double), ("kept", ctypes.c_int64),
                 ("accepted", ctypes.c_int64)]
+
+
+def launch_count() -> int:
+    """Kernel launches the library has issued in this process
+    (sp_launch_count; graph kernels count once per replay)."""
+    return int(_lib().sp_launch_count())
 
 
 def stream_now() -> float:

@@ -164,6 +164,7 @@ struct sp_batch {
     std::vector<cudaEvent_t> ev_t0, ev_t1;     // per group, around its persistent launch (timed runs)
     bool timed_valid = false;
     cudaGraphExec_t graph = nullptr;
+    uint64_t graph_kernels = 0;  // kernels recorded in the graph
     int last_mode = -1;
 };
 
@@ -486,7 +487,9 @@ extern "C" int sp_batch_capture(sp_batch *b, int32_t mode, void *stream) {
         cudaGetLastError();
         return SP_ECUDA;
     }
+    capture_begin();
     const int rc = run_mode(b, mode, s0);
+    const uint64_t kernels = capture_end();
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(s0, &graph);
     if (rc || e != cudaSuccess || !graph) {
@@ -503,12 +506,15 @@ extern "C" int sp_batch_capture(sp_batch *b, int32_t mode, void *stream) {
     }
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = exec;
+    b->graph_kernels = kernels;
     return SP_OK;
 }
 
 extern "C" int sp_batch_launch(sp_batch *b, void *stream) {
     if (!b || !b->graph || !on_device(b)) return SP_EINVAL;
-    return cudaGraphLaunch(b->graph, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? SP_OK : SP_ECUDA;
+    if (cudaGraphLaunch(b->graph, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return SP_ECUDA;
+    note_launch(b->graph_kernels);
+    return SP_OK;
 }
 
 extern "C" int sp_batch_results(sp_batch *b, int32_t beam, sp_cand *h_cands, int64_t cap, int64_t *h_count,

@@ -1,6 +1,7 @@
 // capi.cpp -- argument checking and the extern "C" entry points of
 // libspotlight (declared and documented in include/spotlight.h).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 
@@ -55,6 +56,30 @@ int sps_common(const int32_t *d_dmt, int32_t ndm, int64_t n_out, const int32_t *
 }
 
 }  // namespace
+
+namespace sp {
+namespace {
+std::atomic<uint64_t> g_launches{0};
+thread_local bool t_capturing = false;  // launches go into a graph, not to the GPU
+thread_local uint64_t t_captured = 0;
+}  // namespace
+void note_launch(uint64_t n) {
+    if (t_capturing)
+        t_captured += n;
+    else
+        g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+void capture_begin() {
+    t_capturing = true;
+    t_captured = 0;
+}
+uint64_t capture_end() {
+    t_capturing = false;
+    return t_captured;
+}
+}  // namespace sp
+
+extern "C" uint64_t sp_launch_count(void) { return sp::g_launches.load(std::memory_order_relaxed); }
 
 extern "C" const char *sp_strerror(int code) {
     switch (code) {

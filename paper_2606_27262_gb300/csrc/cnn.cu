@@ -517,6 +517,7 @@ int cnn_gemm(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *
         gemm_nt_kernel<kEpiStore><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, ks, Cf, Cb, ldc, bias);
     else
         gemm_nt_kernel<kEpiAtomic><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, ks, Cf, Cb, ldc, bias);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
@@ -534,6 +535,7 @@ int cnn_im2col(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, 
     } else {
         im2col_kernel<<<grid_for(P * Kp), 256, 0, st>>>(x, Nb, H, W, C, stride, Ho, Wo, Kp, cols);
     }
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
@@ -541,6 +543,7 @@ int cnn_col2im_relu(const float *dcols, const __nv_bfloat16 *x, int Nb, int H, i
                     int Wo, int Kp, __nv_bfloat16 *dz, cudaStream_t st) {
     col2im_relu_kernel<<<grid_for((int64_t)Nb * H * W * C), 256, 0, st>>>(dcols, x, Nb, H, W, C, stride, Ho, Wo, Kp,
                                                                          dz);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
@@ -548,39 +551,46 @@ int cnn_transpose(const __nv_bfloat16 *in, int64_t R, int64_t C, __nv_bfloat16 *
     if ((C + 31) / 32 > 65535) return SP_ELIMIT;
     const dim3 grid((unsigned)((R + 31) / 32), (unsigned)((C + 31) / 32));
     transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(in, R, C, out);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
 int cnn_avgpool(const __nv_bfloat16 *y, int Nb, int HW, int C, float *feat, cudaStream_t st) {
     avgpool_kernel<<<grid_for((int64_t)Nb * C), 256, 0, st>>>(y, Nb, HW, C, feat);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
 int cnn_avgpool_back(const float *dfeat, const __nv_bfloat16 *y, int Nb, int HW, int C, __nv_bfloat16 *dz,
                      cudaStream_t st) {
     avgpool_back_kernel<<<grid_for((int64_t)Nb * HW * C), 256, 0, st>>>(dfeat, y, Nb, HW, C, dz);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
 int cnn_head(const float *feat, int Nb, int C, const float *w, const float *b, float *logit, cudaStream_t st) {
     head_kernel<<<(Nb + 7) / 8, 256, 0, st>>>(feat, Nb, C, w, b, logit);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
 int cnn_fuse_loss(const float *l1, const float *l2, const float *label, int Nb, float *prob, float *dl1, float *dl2,
                   float *loss, cudaStream_t st) {
     fuse_loss_kernel<<<(Nb + 255) / 256, 256, 0, st>>>(l1, l2, label, Nb, prob, dl1, dl2, loss);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
 int cnn_head_back(const float *feat, const float *dl, int Nb, int C, const float *w, float *dfeat, float *dw,
                   float *db, cudaStream_t st) {
     head_back_kernel<<<(C + 255) / 256, 256, 0, st>>>(feat, dl, Nb, C, w, dfeat, dw, db);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
 int cnn_bias_grad(const __nv_bfloat16 *dz, int64_t P, int C, float *db, cudaStream_t st) {
     bias_grad_kernel<<<C, 256, 0, st>>>(dz, P, C, db);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
@@ -588,11 +598,13 @@ int cnn_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, 
              int64_t step, __nv_bfloat16 *wb, cudaStream_t st) {
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     adam_kernel<<<grid_for(n), 256, 0, st>>>(w, g, m, v, n, lr, b1, b2, eps, c1, c2, wb);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
 int cnn_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b, cudaStream_t st) {
     to_bf16_kernel<<<grid_for(n), 256, 0, st>>>(a, n, b);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
@@ -601,6 +613,7 @@ int cnn_extract(const uint8_t *xt, int64_t pitch, int64_t n_in, int32_t nchan, c
                 cudaStream_t st) {
     extract_kernel<<<dim3((unsigned)nsub, (unsigned)ncand), 256, 0, st>>>(xt, pitch, n_in, nchan, delays, cands, wt,
                                                                         nsub, t_in, sub);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
@@ -613,9 +626,12 @@ int cnn_features(const float *sub, int Nb, int S, int T_in, const int32_t *shift
             cudaSuccess)
         return SP_ECUDA;
     features_raw_kernel<<<dim3(kImg / kFeatRows, Nb), kImg, smem, st>>>(sub, T_in, shift, ft_raw, dmt_raw);
+    note_launch();
     if (cudaGetLastError() != cudaSuccess) return SP_ECUDA;
     normalise_kernel<<<Nb, 256, 0, st>>>(ft_raw, ft);
+    note_launch();
     normalise_kernel<<<Nb, 256, 0, st>>>(dmt_raw, dmt);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

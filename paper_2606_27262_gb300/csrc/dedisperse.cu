@@ -517,6 +517,7 @@ int launch_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t
     if (row0 < 0 || row0 >= ring_rows || n_in > ring_rows) return SP_EINVAL;
     const dim3 grid((unsigned)(pitch / kStTime), (unsigned)((nchan + kStChan - 1) / kStChan));
     stage_input_kernel<<<grid, 256, 0, stream>>>(d_in, n_in, nchan, d_staged, pitch, row0, ring_rows);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
@@ -536,6 +537,7 @@ int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, i
                                                           plan->d_tile_first, plan->d_tile_count,
                                                           plan->d_chunk_geo, plan->d_chunk_off, plan->copies_max,
                                                           plan->raw_max, n_out, d_out, plan->d_status);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
@@ -570,6 +572,7 @@ int launch_dedisperse_batch(const BatchLaunch &b, cudaStream_t stream, bool pers
     k.batch<<<(unsigned)grid, k.threads, b.smem_bytes, stream>>>(b.d_beams, b.d_item_begin, b.nbeams, b.nitems,
                                                                  persistent ? b.d_counter : nullptr, b.copies_max,
                                                                  b.raw_max, b.d_status);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

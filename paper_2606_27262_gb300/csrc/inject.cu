@@ -82,5 +82,6 @@ extern "C" int sp_inject_quantised(uint8_t *d_data, const float *d_signal, int64
     v.inv_s2 = 1.0 / (sigma * std::sqrt(2.0));
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
     sp::inject_kernel<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(d_data, d_signal, n, v);
+    sp::note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }

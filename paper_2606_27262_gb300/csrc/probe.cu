@@ -59,6 +59,7 @@ extern "C" int sp_probe_iadd3_rate(int iters, double *iadd3_per_sm_per_clk, int 
     }
     iadd3_probe_kernel<<<nsm, 1024>>>(iters / 8 + 1, 1u, sink, cyc);  // warm-up
     iadd3_probe_kernel<<<nsm, 1024>>>(iters, 12345u, sink, cyc);
+    sp::note_launch(2);
     std::vector<long long> h(nsm);
     int rc = SP_OK;
     if (cudaMemcpy(h.data(), cyc, nsm * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess) rc = SP_ECUDA;

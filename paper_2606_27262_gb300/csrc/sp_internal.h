@@ -158,6 +158,15 @@ inline int64_t align256(int64_t x) { return (x + 255) & ~int64_t(255); }
 bool on_plan_device(const sp_plan *p);
 int check_widths(const int32_t *w, int32_t nw);
 
+// Kernel launches issued by the library (sp_launch_count); every launcher
+// adds its launches, a CUDA-graph replay adds the kernels of the graph.
+// Between capture_begin and capture_end the calling thread's launches are
+// recorded into a graph: they are counted for the graph (capture_end
+// returns how many) instead of as launches.
+void note_launch(uint64_t n = 1);
+void capture_begin();
+uint64_t capture_end();
+
 // Facts about a classifier that the streaming search needs (cnn.cpp).
 int32_t cnn_max_batch(const sp_cnn *c);
 int cnn_device(const sp_cnn *c);

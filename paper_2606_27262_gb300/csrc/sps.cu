@@ -528,6 +528,7 @@ int launch_sps(const SpsArgs &a, cudaStream_t stream) {
     if (rc) return rc;
     sps_stats_kernel<<<dim3((unsigned)a.nblk, (unsigned)a.ndm), 256, 0, stream>>>(a.dmt, a.n_out, a.norm_block,
                                                                                 a.nblk, wl, m0s, coefs);
+    note_launch();
     if (cudaGetLastError() != cudaSuccess) return SP_ECUDA;
     if (cudaMemsetAsync(wide_count, 0, sizeof(int), stream) != cudaSuccess) return SP_ECUDA;
     if (!map && cudaMemsetAsync(a.count, 0, sizeof(int64_t), stream) != cudaSuccess) return SP_ECUDA;
@@ -565,6 +566,7 @@ int launch_sps(const SpsArgs &a, cudaStream_t stream) {
         sps_boxcar_kernel<false><<<grid, 256, boxcar_smem(maxw), stream>>>(b);
         sps_boxcar_wide_kernel<false><<<nsm, 256, boxcar_wide_smem(maxw), stream>>>(b);
     }
+    note_launch(2);
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

@@ -198,14 +198,25 @@ def _held(batch, b):
 
 @pytest.mark.parametrize("mode", [sp.SP_BATCH_GROUPED, sp.SP_BATCH_GROUPED_GRID, sp.SP_BATCH_PER_BEAM])
 def test_batch_graph_replay(mode):
+    """Graph replays give the eager results; the launch counter sees the
+    eager run's kernels once per replay and none at capture (per beam:
+    staging, block statistics, boxcar, 64-bit boxcar pass; dedispersion once
+    per group, or once per beam with per-beam launches)."""
     batch, plans, plan_dms, f, widths, data, bursts = _small_batch(shape=1)
     s = torch.cuda.Stream()
+    per_step = 5 * batch.nbeams if mode == sp.SP_BATCH_PER_BEAM else 4 * batch.nbeams + batch.ngroups
     with torch.cuda.stream(s):
+        lc = sp.launch_count()
         batch.run(mode, stream=s)
+        assert sp.launch_count() - lc == per_step
         eager = [batch.results(b, stream=s) for b in range(batch.nbeams)]
+        lc = sp.launch_count()
         batch.capture(mode, stream=s)
+        assert sp.launch_count() == lc
         for _ in range(2):
+            lc = sp.launch_count()
             batch.launch(stream=s)
+            assert sp.launch_count() - lc == per_step
             for b in range(batch.nbeams):
                 assert np.array_equal(batch.results(b, stream=s), eager[b])
     for b in range(batch.nbeams):

@@ -84,12 +84,21 @@ def test_dedisperse_saturated_input():
 
 
 def test_dedisperse_config1_bitexact():
+    """Also counts the kernels: sp_dedisperse launches two (staging,
+    dedispersion), sp_single_pulse_search three (block statistics, boxcar
+    with peaks, 64-bit boxcar pass)."""
     wl = synth.config1()
     plan = sp.Plan(wl.freqs, wl.tsamp, wl.dms)
     x, _ = synth.make_workload_beam(wl, wl.n_out + plan.max_delay)
-    got = gu.dev_dedisperse(plan, x).cpu().numpy()
+    lc = sp.launch_count()
+    dmt = gu.dev_dedisperse(plan, x)
+    assert sp.launch_count() - lc == 2
+    got = dmt.cpu().numpy()
     want = oracle.dedisperse(x, oracle.delays(wl.freqs, wl.tsamp, wl.dms), wl.n_out)
     assert np.array_equal(got, want)
+    lc = sp.launch_count()
+    gu.dev_candidates(dmt, wl.widths, wl.threshold, wl.norm_block)
+    assert sp.launch_count() - lc == 3
 
 
 def test_shape_errors():

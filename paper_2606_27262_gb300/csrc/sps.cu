@@ -112,7 +112,7 @@ constexpr int kBxIn = kBxRows - 2;
 constexpr int kBxPts = kBxT + 2;          // scored points per row: samples t0-1 .. t0+256
 constexpr int kBxOrg = 4;                 // staged index 0 = sample t0 - 4 (16-byte aligned rows)
 constexpr int kBxFirst = kBxOrg - 1;      // staged index of point 0 (sample t0 - 1)
-constexpr int kBxPass = 9;                // points per thread and pass (16 threads per row)
+constexpr int kBxPass = 8;                // points per thread and pass (16 threads per row)
 
 // Entries of the inclusive prefix Q of one staged row: point i's windows
 // [i, i + w) need Q[i + w - 1] - Q[i - 1], up to i = kBxFirst + kBxPts - 1.
@@ -134,6 +134,23 @@ __device__ __forceinline__ void prefix_row(const int32_t *__restrict__ row, int6
     const int lane = threadIdx.x & 31;
     PT carry = 0;
     for (int base0 = 0; base0 < nq; base0 += 512) {
+        if (nq - base0 <= 16) {  // a last chunk of one lane's width: lane 0 alone, no warp scan
+            if (lane == 0) {
+                PT acc = carry;
+                for (int e = 0; e < nq - base0; ++e) {
+                    const int64_t t = s0 + base0 + e;
+                    int32_t x = 0;
+                    if (t >= 0 && t < n_out) {
+                        x = __ldg(row + t);
+                        vmin = min(vmin, x);
+                        vmax = max(vmax, x);
+                    }
+                    acc += (PT)x;
+                    Q[base0 + e] = acc;
+                }
+            }
+            break;
+        }
         const int base = base0 + lane * 16;
         int32_t v[16];
         const int64_t t = s0 + base;
@@ -184,54 +201,66 @@ __device__ __forceinline__ void prefix_row(const int32_t *__restrict__ row, int6
     }
 }
 
+// Normalisation block of sample t >= 0 (32-bit division when both fit).
 __device__ __forceinline__ int64_t block_of(int64_t t, int64_t norm_block, int64_t nblk) {
-    int64_t b = norm_block > 0 ? t / norm_block : 0;
+    int64_t b;
+    if (norm_block <= 0)
+        b = 0;
+    else if (t <= INT32_MAX && norm_block <= INT32_MAX)
+        b = (int64_t)((uint32_t)t / (uint32_t)norm_block);
+    else
+        b = t / norm_block;
     return b > nblk - 1 ? nblk - 1 : b;
 }
 
-// Phase 2 for the points p = l + 16 (j0 + j), j < kBxPass, of one staged
-// row: best S/N over the widths and its width index.
-template <typename PT>
-__device__ __forceinline__ void score_pass(const PT *Q, int d, int64_t s0, int64_t n_out, int fit_end, int l, int j0,
-                                           const WidthList &wl, int64_t norm_block, int64_t nblk,
-                                           const int32_t *__restrict__ m0s, const float2 *__restrict__ coefs,
-                                           float *snr_row, int8_t *k_row) {
-    float best[kBxPass];
-    int kb[kBxPass];
+// Phase 2 for the points p = p0 + 16 j, j < NP (those with p < kBxPts), of
+// one staged row: best S/N over the widths and its width index.
+// `interior`: every point of the tile is a sample of the beam; `tile_block`:
+// the one normalisation block of all of them, or -1.
+template <typename PT, int NP>
+__device__ __forceinline__ void score_points(const PT *Q, int d, int64_t s0, int64_t n_out, int fit_end, int p0,
+                                             bool interior, int64_t tile_block, const WidthList &wl,
+                                             int64_t norm_block, int64_t nblk, const int32_t *__restrict__ m0s,
+                                             const float2 *__restrict__ coefs, float *snr_row, int8_t *k_row) {
+    float best[NP];
+    int kb[NP];
 #pragma unroll
-    for (int j = 0; j < kBxPass; ++j) {
+    for (int j = 0; j < NP; ++j) {
         best[j] = -INFINITY;
         kb[j] = -1;
     }
-    // valid points of this pass: sample t in [0, n_out)
-    int jlo = kBxPass, jhi = -1;
+    // valid points: p < kBxPts and sample t in [0, n_out)
+    int jlo = NP, jhi = -1;
 #pragma unroll
-    for (int j = 0; j < kBxPass; ++j) {
-        const int p = l + 16 * (j0 + j);
+    for (int j = 0; j < NP; ++j) {
+        const int p = p0 + 16 * j;
         const int64_t t = s0 + kBxFirst + p;
-        if (p < kBxPts && t >= 0 && t < n_out) {
+        if (p < kBxPts && (interior || (t >= 0 && t < n_out))) {
             jlo = min(jlo, j);
             jhi = max(jhi, j);
         }
     }
     if (jhi >= 0) {
-        const int64_t t_lo = s0 + kBxFirst + l + 16 * (j0 + jlo), t_hi = s0 + kBxFirst + l + 16 * (j0 + jhi);
-        const int64_t b_lo = block_of(t_lo, norm_block, nblk), b_hi = block_of(t_hi, norm_block, nblk);
+        const int64_t t_lo = s0 + kBxFirst + p0 + 16 * jlo, t_hi = s0 + kBxFirst + p0 + 16 * jhi;
+        const int64_t b_lo = tile_block >= 0 ? tile_block : block_of(t_lo, norm_block, nblk);
+        const int64_t b_hi = tile_block >= 0 ? tile_block : block_of(t_hi, norm_block, nblk);
         const int64_t row_blk = (int64_t)d * nblk;
-        const int i_last = kBxFirst + l + 16 * (j0 + jhi);
-        if (b_lo == b_hi && jlo == 0 && jhi == kBxPass - 1 && i_last + wl.w[wl.nw - 1] <= fit_end) {
+        const int i_last = kBxFirst + p0 + 16 * jhi;
+        if (b_lo == b_hi && jlo == 0 && jhi == NP - 1 && i_last + wl.w[wl.nw - 1] <= fit_end) {
             // every point valid, every window inside the beam, one block
             const PT m0 = (PT)(int64_t)__ldg(m0s + row_blk + b_lo);
-            PT q0[kBxPass];
+            const float2 *cfs = coefs + (row_blk + b_lo) * wl.nw;
+            PT q0[NP];
 #pragma unroll
-            for (int j = 0; j < kBxPass; ++j) q0[j] = Q[kBxFirst + l + 16 * (j0 + j) - 1];
+            for (int j = 0; j < NP; ++j) q0[j] = Q[kBxFirst + p0 + 16 * j - 1];
             for (int k = 0; k < wl.nw; ++k) {
                 const int w = wl.w[k];
                 const PT cw = (PT)w * m0;
-                const float2 cf = __ldg(coefs + (row_blk + b_lo) * wl.nw + k);
+                const float2 cf = __ldg(cfs + k);
+                const PT *Qw = Q + kBxFirst + p0 + w - 1;
 #pragma unroll
-                for (int j = 0; j < kBxPass; ++j) {
-                    const PT xs = Q[kBxFirst + l + 16 * (j0 + j) + w - 1] - q0[j] - cw;
+                for (int j = 0; j < NP; ++j) {
+                    const PT xs = Qw[16 * j] - q0[j] - cw;
                     const float xf = sizeof(PT) == 4 ? (float)(int32_t)xs : (float)(int64_t)xs;
                     const float sv = fmaf(xf, cf.x, -cf.y);
                     if (sv > best[j]) {
@@ -248,8 +277,8 @@ __device__ __forceinline__ void score_pass(const PT *Q, int d, int64_t s0, int64
                 const float2 cf = __ldg(coefs + (row_blk + b_lo) * wl.nw + k);
                 bool any = false;
 #pragma unroll
-                for (int j = 0; j < kBxPass; ++j) {
-                    const int i = kBxFirst + l + 16 * (j0 + j);
+                for (int j = 0; j < NP; ++j) {
+                    const int i = kBxFirst + p0 + 16 * j;
                     if (j < jlo || j > jhi || i + w > fit_end) continue;
                     any = true;
                     const PT xs = Q[i + w - 1] - Q[i - 1] - cw;
@@ -267,8 +296,8 @@ __device__ __forceinline__ void score_pass(const PT *Q, int d, int64_t s0, int64
                 const int w = wl.w[k];
                 bool any = false;
 #pragma unroll
-                for (int j = 0; j < kBxPass; ++j) {
-                    const int i = kBxFirst + l + 16 * (j0 + j);
+                for (int j = 0; j < NP; ++j) {
+                    const int i = kBxFirst + p0 + 16 * j;
                     if (j < jlo || j > jhi || i + w > fit_end) continue;
                     any = true;
                     const int64_t b = block_of(s0 + i, norm_block, nblk);
@@ -287,8 +316,8 @@ __device__ __forceinline__ void score_pass(const PT *Q, int d, int64_t s0, int64
         }
     }
 #pragma unroll
-    for (int j = 0; j < kBxPass; ++j) {
-        const int p = l + 16 * (j0 + j);
+    for (int j = 0; j < NP; ++j) {
+        const int p = p0 + 16 * j;
         if (p < kBxPts) {
             snr_row[p] = best[j];
             k_row[p] = (int8_t)kb[j];
@@ -332,6 +361,12 @@ __device__ __forceinline__ bool boxcar_tile(const BoxcarArgs &a, int tx, int ty,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool vec = a.vec;
     const int fit_end = (int)min(a.n_out - s0, (int64_t)INT32_MAX);
+    // The tile's scored samples [ts, te] inside the beam and their blocks.
+    const int64_t ts = max(s0 + kBxFirst, (int64_t)0), te = min(s0 + kBxFirst + kBxPts, a.n_out) - 1;
+    const bool interior = s0 + kBxFirst >= 0 && s0 + kBxFirst + kBxPts <= a.n_out;
+    const int64_t bs = ts <= te ? block_of(ts, a.norm_block, a.nblk) : 0;
+    const int64_t be = ts <= te ? block_of(te, a.norm_block, a.nblk) : -1;
+    const int64_t tile_block = bs == be ? bs : -1;
 
     bool wide = false;
     for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
@@ -346,9 +381,7 @@ __device__ __forceinline__ bool boxcar_tile(const BoxcarArgs &a, int tx, int ty,
                 vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
             }
             if (vmin <= vmax) {
-                const int64_t ts = max(s0 + kBxFirst, (int64_t)0), te = min(s0 + kBxFirst + kBxPts, a.n_out) - 1;
                 if (ts <= te) {
-                    const int64_t bs = block_of(ts, a.norm_block, a.nblk), be = block_of(te, a.norm_block, a.nblk);
                     for (int64_t b = bs + lane; b <= be; b += 32) {
                         const int64_t m0 = __ldg(a.m0s + (int64_t)d * a.nblk + b);
                         const int64_t dev = max((int64_t)vmax - m0, m0 - (int64_t)vmin);
@@ -372,9 +405,15 @@ __device__ __forceinline__ bool boxcar_tile(const BoxcarArgs &a, int tx, int ty,
             }
         } else {
             const PT *Q = Qs + (size_t)rr * nq;
-            score_pass<PT>(Q, d, s0, a.n_out, fit_end, l, 0, a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
-            score_pass<PT>(Q, d, s0, a.n_out, fit_end, l, kBxPass, a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow,
-                           krow);
+            // points l + 16 j: two passes of eight over p < 256, then the
+            // last two points (256, 257) on threads l = 0, 1
+            score_points<PT, kBxPass>(Q, d, s0, a.n_out, fit_end, l, interior, tile_block, a.wl, a.norm_block,
+                                      a.nblk, a.m0s, a.coefs, srow, krow);
+            score_points<PT, kBxPass>(Q, d, s0, a.n_out, fit_end, l + 16 * kBxPass, interior, tile_block, a.wl,
+                                      a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
+            if (l < kBxPts - 32 * kBxPass)
+                score_points<PT, 1>(Q, d, s0, a.n_out, fit_end, l + 32 * kBxPass, interior, tile_block, a.wl,
+                                    a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
         }
     }
     __syncthreads();

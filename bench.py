@@ -195,14 +195,15 @@ def kernel_source_hash() -> str:
     return hashlib.sha256(open(DEDISP_SRC, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic(adds_per_launch: float):
+def profiled_traffic(n_out: int):
     """DRAM bytes per launch of the dedispersion kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
+    summary of the full single-beam workload, or None when the kernel source
+    changed since the capture or another length is being measured."""
     try:
         prof = json.load(open(PROFILE_JSON))
     except (OSError, ValueError):
         return None
-    if prof.get("kernel_source_sha256_16") != kernel_source_hash():
+    if prof.get("kernel_source_sha256_16") != kernel_source_hash() or int(n_out) != int(prof.get("n_out", -1)):
         return None
     return float(prof["dram_bytes_per_launch_full_config"])
 
@@ -344,7 +345,7 @@ def run_ours(args):
         "stage_ms": {"stage_input": tr_ms, "dedisperse": dd_ms, "single_pulse_search": sps_ms},
         "candidates_per_beam": ncand,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(adds),
+                     "frac": achieved / peak, "traffic": profiled_traffic(wl.n_out),
                      "kernel": "dedisperse_kernel",
                      "peak_basis": f"{nsm} SMs x {lanes:.1f} measured 32-bit add lanes/SM/clk x "
                                    f"{MAX_SM_MHZ:.0f} MHz"},

@@ -95,8 +95,9 @@ def parse_args(argv=None):
     p.add_argument("--dmt-budget-gb", type=float, default=24.0,
                    help="batched workload: DM-transform bytes per group arena (GB)")
     p.add_argument("--no-per-beam", action="store_true", help="batched workload: skip the comparisons")
-    p.add_argument("--batch-mode", choices=["persistent", "grid"], default="persistent",
-                   help="batched workload: dedispersion launch style of the timed step")
+    p.add_argument("--batch-mode", choices=["persistent", "grid"], default="grid",
+                   help="batched workload: dedispersion launch style of the timed step (grid: one CTA per "
+                        "work item; persistent: a resident grid draining a work queue)")
     return p.parse_args(argv)
 
 
@@ -477,7 +478,8 @@ def run_batched(args):
         "speedup_vs_per_beam": (per_beam["ms_per_step"] / ms_step) if per_beam else None,
         "candidates": int(sum(counts)),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "dedisperse_batch_kernel",
+                     "traffic": None,
+                     "kernel": "dedisperse_items_kernel" if args.batch_mode == "grid" else "dedisperse_batch_kernel",
                      "kernel_ms_per_step": dd_ms,
                      "peak_basis": f"{nsm} SMs x {lanes:.1f} measured 32-bit add lanes/SM/clk x "
                                    f"{MAX_SM_MHZ:.0f} MHz"},

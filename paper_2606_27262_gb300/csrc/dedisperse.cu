@@ -417,13 +417,51 @@ dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, 
     if (!ok && threadIdx.x == 0) atomicOr(status, SP_STATUS_STAGING_TIMEOUT);
 }
 
-// Many beams in one launch.  Items are (beam, DM tile, time tile), numbered
+// Last beam whose first item is <= item.
+__device__ __forceinline__ int beam_of(const int64_t *__restrict__ item_begin, int32_t nbeams, int64_t item) {
+    int lo = 0, hi = nbeams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(item_begin + mid) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Many beams in one launch, one item per CTA (item = blockIdx.x): the grid
+// kernel's body after a lookup of the item's beam.  CTAs retire, so the
+// block scheduler can interleave other kernels' CTAs (a search, a
+// classifier) between them.  Items are (beam, DM tile, time tile), numbered
 // beam by beam and, within a beam, in the raster order of the grid kernel;
 // beams may differ in length, DM list and channel count but share the kernel
-// shape.  Persistent (counter != nullptr): each CTA takes items from a work
-// queue (one atomic per item) until it is empty.  Otherwise one item per
-// CTA (item = blockIdx.x), so that CTAs retire and the block scheduler can
-// interleave other kernels' CTAs between them.
+// shape.
+template <int CH, int SPT>
+__global__ void __launch_bounds__(CH * 32, (CH == 8 ? 2 : 3))
+dedisperse_items_kernel(const BatchBeamDev *__restrict__ beams, const int64_t *__restrict__ item_begin,
+                        int32_t nbeams, int64_t nitems, int32_t copies_max, int32_t raw_max,
+                        int32_t *__restrict__ status) {
+    using S = Shape<CH, SPT>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int64_t item = blockIdx.x;
+    if (item >= nitems) return;
+    const int b = beam_of(item_begin, nbeams, item);
+    const BatchBeamDev bm = beams[b];
+    int tile;
+    int64_t tq;
+    raster(item - __ldg(item_begin + b), bm.ntiles, (int64_t)bm.ntime, S::GROUP, tile, tq);
+    init_barriers<CH, SPT>(smem);
+    const bool ok = dedisp_tile<CH, SPT>(smem, 0u, bm.xt, bm.pitch, bm.nchan, bm.nchunks, __ldg(bm.tile_first + tile),
+                                         __ldg(bm.tile_count + tile), tq * S::T,
+                                         bm.geo + (int64_t)tile * bm.nchunks * CH,
+                                         bm.off + (int64_t)tile * bm.nchunks * CH * S::DT, copies_max, raw_max,
+                                         bm.n_out, bm.out);
+    if (!ok && threadIdx.x == 0) atomicOr(status, SP_STATUS_STAGING_TIMEOUT);
+}
+
+// The same items from a persistent grid: each CTA takes items from a work
+// queue (one atomic per item) until it is empty; its mbarrier phases carry
+// over from item to item.  (counter == nullptr: one item per CTA, as the
+// items kernel, in this kernel's loop.)
 template <int CH, int SPT>
 __global__ void __launch_bounds__(CH * 32, (CH == 8 ? 2 : 3))
 dedisperse_batch_kernel(const BatchBeamDev *__restrict__ beams, const int64_t *__restrict__ item_begin,
@@ -443,12 +481,7 @@ dedisperse_batch_kernel(const BatchBeamDev *__restrict__ beams, const int64_t *_
         __syncthreads();
         const int64_t item = *s_item;  // thread 0 rewrites it only after the tile's barriers
         if (item >= nitems) break;
-        int lo = 0, hi = nbeams - 1;  // last beam whose first item is <= item
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(item_begin + mid) <= item) lo = mid;
-            else hi = mid - 1;
-        }
+        const int lo = beam_of(item_begin, nbeams, item);
         const BatchBeamDev &bm = beams[lo];
         const int32_t nchunks = bm.nchunks;
         int tile;
@@ -471,15 +504,18 @@ using GridKernel = void (*)(const uint8_t *, int64_t, int32_t, int32_t, const in
                             const int4 *, const int32_t *, int32_t, int32_t, int64_t, int32_t *, int32_t *);
 using BatchKernel = void (*)(const BatchBeamDev *, const int64_t *, int32_t, int64_t, unsigned long long *, int32_t,
                              int32_t, int32_t *);
+using ItemsKernel = void (*)(const BatchBeamDev *, const int64_t *, int32_t, int64_t, int32_t, int32_t, int32_t *);
 struct ShapeKernels {
     GridKernel grid;
     BatchKernel batch;
+    ItemsKernel items;
     int threads;
     int time_tile;
 };
 template <int CH, int SPT>
 constexpr ShapeKernels shape_kernels() {
-    return {dedisperse_kernel<CH, SPT>, dedisperse_batch_kernel<CH, SPT>, CH * 32, Shape<CH, SPT>::T};
+    return {dedisperse_kernel<CH, SPT>, dedisperse_batch_kernel<CH, SPT>, dedisperse_items_kernel<CH, SPT>, CH * 32,
+            Shape<CH, SPT>::T};
 }
 static_assert(kDedispNumShapes == 3 && kDedispShapeCh[0] == 8 && kDedispShapeSpt[0] == 16 &&
                   kDedispShapeCh[1] == 8 && kDedispShapeSpt[1] == 8 && kDedispShapeCh[2] == 4 &&
@@ -501,6 +537,8 @@ int configure_shape(int shape, int smem_bytes) {
     if (cudaFuncSetAttribute(kShapes[shape].grid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
             cudaSuccess ||
         cudaFuncSetAttribute(kShapes[shape].batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(kShapes[shape].items, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
             cudaSuccess) {
         cudaGetLastError();
         return SP_ECUDA;
@@ -569,9 +607,12 @@ int launch_dedisperse_batch(const BatchLaunch &b, cudaStream_t stream, bool pers
     } else if (grid > INT32_MAX) {
         return SP_ELIMIT;
     }
-    k.batch<<<(unsigned)grid, k.threads, b.smem_bytes, stream>>>(b.d_beams, b.d_item_begin, b.nbeams, b.nitems,
-                                                                 persistent ? b.d_counter : nullptr, b.copies_max,
-                                                                 b.raw_max, b.d_status);
+    if (persistent)
+        k.batch<<<(unsigned)grid, k.threads, b.smem_bytes, stream>>>(b.d_beams, b.d_item_begin, b.nbeams, b.nitems,
+                                                                     b.d_counter, b.copies_max, b.raw_max, b.d_status);
+    else
+        k.items<<<(unsigned)grid, k.threads, b.smem_bytes, stream>>>(b.d_beams, b.d_item_begin, b.nbeams, b.nitems,
+                                                                     b.copies_max, b.raw_max, b.d_status);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }

@@ -57,9 +57,12 @@ def test_single_rank_helpers():
 
 def test_profiled_traffic_guard(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "PROFILE_JSON", str(tmp_path / "p.json"))
-    assert bench.profiled_traffic(1.0) is None
-    (tmp_path / "p.json").write_text('{"kernel_source_sha256_16": "stale", "dram_bytes_per_launch_full_config": 5}')
-    assert bench.profiled_traffic(1.0) is None
+    assert bench.profiled_traffic(131072) is None
+    (tmp_path / "p.json").write_text('{"kernel_source_sha256_16": "stale", "n_out": 131072, '
+                                     '"dram_bytes_per_launch_full_config": 5}')
+    assert bench.profiled_traffic(131072) is None
     h = bench.kernel_source_hash()
-    (tmp_path / "p.json").write_text('{"kernel_source_sha256_16": "%s", "dram_bytes_per_launch_full_config": 5}' % h)
-    assert bench.profiled_traffic(1.0) == 5.0
+    (tmp_path / "p.json").write_text('{"kernel_source_sha256_16": "%s", "n_out": 131072, '
+                                     '"dram_bytes_per_launch_full_config": 5}' % h)
+    assert bench.profiled_traffic(131072) == 5.0
+    assert bench.profiled_traffic(16384) is None  # another workload length

@@ -347,7 +347,9 @@ int sp_searcher_run_host(sp_searcher *s, const uint8_t *h_in, sp_cand *h_cands, 
  *   run, the last beam of a per-beam run); else SP_EINVAL.
  * sp_batch_run_host: end to end from host memory: copies h_in[b] (n_in *
  *   nchan bytes each; page-locked memory makes the copies asynchronous) into
- *   the beams' inputs, runs SP_BATCH_GROUPED, then copies every beam's count
+ *   the beams' inputs group by group on a copy stream of the batch (group
+ *   g + 1's copies overlap group g's work; each group waits only for its
+ *   own), runs SP_BATCH_GROUPED, then copies every beam's count
  *   to h_counts [nbeams] and its first min(count, cap_per_beam, cand_cap)
  *   candidates to h_cands + b * cap_per_beam.  Synchronises `stream`;
  *   SP_EOVERFLOW (after copying) if any beam overflowed.

@@ -160,6 +160,8 @@ struct sp_batch {
     int64_t device_bytes = 0;
     // Execution.
     cudaStream_t side = nullptr;               // search stream of the grouped mode
+    cudaStream_t copy = nullptr;               // host input copies of sp_batch_run_host
+    std::vector<cudaEvent_t> ev_in;            // per group: its beams' inputs are on the device
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_dd[2] = {nullptr, nullptr}, ev_sps[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> ev_t0, ev_t1;     // per group, around its persistent launch (timed runs)
     bool timed_valid = false;
@@ -176,7 +178,9 @@ void batch_free(sp_batch *b) {
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : b->ev_t0) if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : b->ev_t1) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_in) if (e) cudaEventDestroy(e);
     if (b->side) cudaStreamDestroy(b->side);
+    if (b->copy) cudaStreamDestroy(b->copy);
     cudaFree(b->d_in);
     cudaFree(b->d_staged[0]);
     cudaFree(b->d_staged[1]);
@@ -220,13 +224,29 @@ int search_beam(sp_batch *b, int32_t beam, const int32_t *dmt, cudaStream_t st) 
     return launch_sps(a, st);
 }
 
-int run_grouped(sp_batch *b, cudaStream_t s0, bool timed, bool persistent) {
+// h_in != nullptr: the beams' inputs come from host memory first, group by
+// group on the copy stream, so that group g + 1's copies overlap group g's
+// work and each group waits only for its own.
+int run_grouped(sp_batch *b, cudaStream_t s0, bool timed, bool persistent, const uint8_t *const *h_in = nullptr) {
     if (cudaEventRecord(b->ev_fork, s0) != cudaSuccess || cudaStreamWaitEvent(b->side, b->ev_fork, 0) != cudaSuccess)
         return SP_ECUDA;
+    if (h_in) {
+        if (cudaStreamWaitEvent(b->copy, b->ev_fork, 0) != cudaSuccess) return SP_ECUDA;
+        for (size_t g = 0; g < b->groups.size(); ++g) {
+            for (int32_t beam = b->groups[g].first; beam < b->groups[g].last; ++beam) {
+                const size_t bytes = (size_t)(b->n_in[beam] * plan_of(b, beam)->nchan);
+                if (cudaMemcpyAsync(b->d_in + b->in_off[beam], h_in[beam], bytes, cudaMemcpyHostToDevice, b->copy) !=
+                    cudaSuccess)
+                    return SP_ECUDA;
+            }
+            if (cudaEventRecord(b->ev_in[g], b->copy) != cudaSuccess) return SP_ECUDA;
+        }
+    }
     for (size_t g = 0; g < b->groups.size(); ++g) {
         const sp_batch::Group &G = b->groups[g];
         const int slot = (int)(g & 1);
         if (g >= 2 && cudaStreamWaitEvent(s0, b->ev_sps[slot], 0) != cudaSuccess) return SP_ECUDA;
+        if (h_in && cudaStreamWaitEvent(s0, b->ev_in[g], 0) != cudaSuccess) return SP_ECUDA;
         for (int32_t beam = G.first; beam < G.last; ++beam) {
             const int rc = launch_stage_input(b->d_in + b->in_off[beam], b->n_in[beam], plan_of(b, beam)->nchan,
                                               b->d_staged[slot] + b->staged_off[beam], b->pitch[beam], s0);
@@ -414,6 +434,7 @@ extern "C" int sp_batch_create(const sp_plan *const *plans, int32_t nplans, cons
     int prio_lo = 0, prio_hi = 0;  // the search stream gets the device's highest priority
     if (!rc && (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
                 cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&b->copy, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&b->ev_dd[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -426,8 +447,10 @@ extern "C" int sp_batch_create(const sp_plan *const *plans, int32_t nplans, cons
     if (!rc) {
         b->ev_t0.assign(b->groups.size(), nullptr);
         b->ev_t1.assign(b->groups.size(), nullptr);
+        b->ev_in.assign(b->groups.size(), nullptr);
         for (size_t g = 0; g < b->groups.size() && !rc; ++g)
-            if (cudaEventCreate(&b->ev_t0[g]) != cudaSuccess || cudaEventCreate(&b->ev_t1[g]) != cudaSuccess) {
+            if (cudaEventCreate(&b->ev_t0[g]) != cudaSuccess || cudaEventCreate(&b->ev_t1[g]) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->ev_in[g], cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
                 rc = SP_ECUDA;
             }
@@ -558,13 +581,11 @@ extern "C" int sp_batch_run_host(sp_batch *b, const uint8_t *const *h_in, sp_can
     if (!b || !h_in || !h_counts || cap_per_beam < 0 || (cap_per_beam > 0 && !h_cands) || !on_device(b))
         return SP_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    for (int32_t beam = 0; beam < b->nbeams; ++beam) {
+    for (int32_t beam = 0; beam < b->nbeams; ++beam)
         if (!h_in[beam]) return SP_EINVAL;
-        const size_t bytes = (size_t)(b->n_in[beam] * plan_of(b, beam)->nchan);
-        if (cudaMemcpyAsync(b->d_in + b->in_off[beam], h_in[beam], bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-            return SP_ECUDA;
-    }
-    int rc = run_mode(b, SP_BATCH_GROUPED, st);
+    int rc = run_grouped(b, st, false, true, h_in);
+    b->last_mode = rc ? b->last_mode : SP_BATCH_GROUPED;
+    b->timed_valid = false;
     if (rc) return rc;
     if (cudaMemcpyAsync(h_counts, b->d_counts, (size_t)b->nbeams * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)

@@ -225,11 +225,18 @@ def test_batch_graph_replay(mode):
         gu.check_candidates(eager[b], o, ob, 6.0)
 
 
-def test_batch_run_host():
-    batch, plans, plan_dms, f, widths, data, bursts = _small_batch(budget=1 << 40)
-    assert batch.ngroups == 1
+@pytest.mark.parametrize("one_group", [True, False])
+def test_batch_run_host(one_group):
+    """End to end from host memory (inputs copied group by group on the
+    batch's copy stream): the device inputs are cleared first, and every
+    beam's candidates equal the device-resident run's."""
+    batch, plans, plan_dms, f, widths, data, bursts = _small_batch(budget=(1 << 40) if one_group else None)
+    assert (batch.ngroups == 1) == one_group
     batch.run(sp.SP_BATCH_GROUPED)
     dev = [batch.results(b) for b in range(batch.nbeams)]
+    for b in range(batch.nbeams):
+        batch.input_tensor(b, data[b].shape[1]).zero_()
+    torch.cuda.synchronize()
     cap = 1 << 16
     hc = np.zeros((batch.nbeams * cap, 4), np.int32)
     pinned = [torch.from_numpy(x).pin_memory() for x in data]
@@ -237,9 +244,10 @@ def test_batch_run_host():
     for b in range(batch.nbeams):
         got = sp.cands_to_numpy(hc[b * cap:(b + 1) * cap], int(counts[b]))
         assert np.array_equal(got, dev[b])
-        dms = plan_dms[batch.beam_plan[b]]
-        want = oracle.dedisperse(data[b], oracle.delays(f, synth.TSAMP, dms), int(batch.n_out[b]))
-        assert np.array_equal(batch.dmt_tensor(b, dms.size).cpu().numpy(), want)
+        if _held(batch, b):
+            dms = plan_dms[batch.beam_plan[b]]
+            want = oracle.dedisperse(data[b], oracle.delays(f, synth.TSAMP, dms), int(batch.n_out[b]))
+            assert np.array_equal(batch.dmt_tensor(b, dms.size).cpu().numpy(), want)
 
 
 def test_batch_create_errors():

@@ -52,6 +52,7 @@ struct sp_cnn {
     Branch br[2];
     __nv_bfloat16 *dzT = nullptr, *colsT = nullptr, *wT = nullptr;
     float *dcols = nullptr, *prob = nullptr, *loss = nullptr;
+    float *bias_part = nullptr;  // [kBiasChunks][256] partial bias gradients
     int64_t step = 0;
     bool have_grads = false;
 };
@@ -135,6 +136,7 @@ void free_cnn(sp_cnn *c) {
     cudaFree(c->colsT);
     cudaFree(c->wT);
     cudaFree(c->dcols);
+    cudaFree(c->bias_part);
     cudaFree(c->prob);
     cudaFree(c->loss);
 }
@@ -192,7 +194,7 @@ int backward(sp_cnn *c, int B, cudaStream_t st) {
         for (int l = kLayers - 1; l >= 0 && !rc; --l) {
             const int Ho = ho_of(l), Kp = kp_of(l), Co = kCout[l];
             const int64_t P = (int64_t)B * Ho * Ho;
-            rc = cnn_bias_grad(b.dz[l], P, Co, b.grads + b.off_b[l], st);
+            rc = cnn_bias_grad(b.dz[l], P, Co, b.grads + b.off_b[l], c->bias_part, st);
             // dW [Co][Kp] = dz^T [Co][P] * cols [P][Kp], split over P.
             if (!rc) rc = cnn_transpose(b.dz[l], P, Co, c->dzT, st);
             if (!rc) rc = cnn_transpose(b.cols[l], P, Kp, c->colsT, st);
@@ -269,6 +271,7 @@ extern "C" int sp_cnn_create(int32_t max_batch, uint64_t seed, sp_cnn **out) {
     if (!rc) rc = dalloc((void **)&c->colsT, cols_max * 2);
     if (!rc) rc = dalloc((void **)&c->wT, (int64_t)kp_of(kLayers - 1) * kCout[kLayers - 1] * 2);
     if (!rc) rc = dalloc((void **)&c->dcols, dcols_max * 4);
+    if (!rc) rc = dalloc((void **)&c->bias_part, (int64_t)kBiasChunks * 256 * 4);
     if (!rc) rc = dalloc((void **)&c->prob, B * 4);
     if (!rc) rc = dalloc((void **)&c->loss, 4);
     // He-normal convolution weights, zero biases, small head weights.

@@ -21,6 +21,7 @@
 //   plus average pooling, the linear heads, the fused loss and Adam.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "sp_cnn_internal.h"
@@ -255,6 +256,52 @@ __global__ void col2im_relu_kernel(const float *__restrict__ dcols, const __nv_b
     }
 }
 
+// The same for C % 8 == 0: one thread per (pixel, 8 channels), 32-bit
+// indices, 16-byte loads of the ReLU input and stores of dz, two 16-byte
+// loads per tap of dcols; taps added in the same order (ky, then kx).
+__global__ void col2im_relu_vec_kernel(const float *__restrict__ dcols, const __nv_bfloat16 *__restrict__ x, int H,
+                                       int W, int C, int stride, int Ho, int Wo, int Kp, uint32_t total,
+                                       __nv_bfloat16 *__restrict__ dz) {
+    const uint32_t cg = (uint32_t)C / 8u;
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const uint32_t pix = idx / cg, c0 = (idx - pix * cg) * 8u;
+        const uint32_t t = pix / (uint32_t)W, w = pix - t * (uint32_t)W;
+        const uint32_t n = t / (uint32_t)H, h = t - n * (uint32_t)H;
+        const uint4 xv = *reinterpret_cast<const uint4 *>(x + (size_t)pix * C + c0);
+        const __nv_bfloat16 *xb = reinterpret_cast<const __nv_bfloat16 *>(&xv);
+        float s[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) s[e] = 0.f;
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) any = any || __bfloat162float(xb[e]) > 0.f;
+        if (any) {
+            for (int ky = 0; ky < 3; ++ky) {
+                const int hh = (int)h + 1 - ky;
+                if (hh < 0 || hh % stride) continue;
+                const int ho = hh / stride;
+                if (ho >= Ho) continue;
+                for (int kx = 0; kx < 3; ++kx) {
+                    const int ww = (int)w + 1 - kx;
+                    if (ww < 0 || ww % stride) continue;
+                    const int wo = ww / stride;
+                    if (wo >= Wo) continue;
+                    const float4 *src = reinterpret_cast<const float4 *>(
+                        dcols + ((size_t)((n * (uint32_t)Ho + (uint32_t)ho) * (uint32_t)Wo + (uint32_t)wo)) * Kp +
+                        (ky * 3 + kx) * C + c0);
+                    const float4 a = src[0], b = src[1];
+                    s[0] += a.x; s[1] += a.y; s[2] += a.z; s[3] += a.w;
+                    s[4] += b.x; s[5] += b.y; s[6] += b.z; s[7] += b.w;
+                }
+            }
+        }
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) o[e] = __float2bfloat16(__bfloat162float(xb[e]) > 0.f ? s[e] : 0.f);
+        *reinterpret_cast<uint4 *>(dz + (size_t)pix * C + c0) = *reinterpret_cast<const uint4 *>(o);
+    }
+}
+
 __global__ void transpose_kernel(const __nv_bfloat16 *__restrict__ in, int64_t R, int64_t C,
                                  __nv_bfloat16 *__restrict__ out) {
     __shared__ __nv_bfloat16 t[32][33];
@@ -352,18 +399,35 @@ __global__ void head_back_kernel(const float *__restrict__ feat, const float *__
 }
 
 // db[c] += sum over rows of dz[.][c] (bias gradient of a conv layer).
-__global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dz, int64_t P, int C, float *__restrict__ db) {
-    const int c = blockIdx.x;
-    float s = 0.f;
-    for (int64_t p = threadIdx.x; p < P; p += blockDim.x) s += __bfloat162float(dz[p * C + c]);
+// Bias gradients db[c] += sum over the P rows of dz[p][c], in two
+// deterministic stages.  Stage 1: chunk blockIdx.x of rows; thread t sums
+// channel t % C over rows t / C + k * (256 / C) (consecutive threads read
+// consecutive bytes of a row), then the 256 / C row lanes are added in a
+// fixed order into part[chunk][c].  Stage 2: one thread per channel adds the
+// chunks in order.  C divides 256.
+__global__ void __launch_bounds__(256) bias_grad_part_kernel(const __nv_bfloat16 *__restrict__ dz, int64_t P, int C,
+                                                             int64_t rows_per_chunk, float *__restrict__ part) {
     __shared__ float red[256];
+    const int c = threadIdx.x % C, rl = threadIdx.x / C, lanes = 256 / C;
+    const int64_t p0 = (int64_t)blockIdx.x * rows_per_chunk;
+    const int64_t p1 = min(P, p0 + rows_per_chunk);
+    float s = 0.f;
+    for (int64_t p = p0 + rl; p < p1; p += lanes) s += __bfloat162float(dz[p * C + c]);
     red[threadIdx.x] = s;
     __syncthreads();
-    for (int o = blockDim.x / 2; o; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    if ((int)threadIdx.x < C) {
+        float t = 0.f;
+        for (int r = 0; r < lanes; ++r) t += red[r * C + threadIdx.x];
+        part[(int64_t)blockIdx.x * C + threadIdx.x] = t;
     }
-    if (threadIdx.x == 0) db[c] += red[0];
+}
+
+__global__ void bias_grad_sum_kernel(const float *__restrict__ part, int nchunk, int C, float *__restrict__ db) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (int k = 0; k < nchunk; ++k) s += part[(int64_t)k * C + c];
+    db[c] += s;
 }
 
 // Adam on fp32 master weights; bf16 copy refreshed for the GEMMs.
@@ -541,8 +605,15 @@ int cnn_im2col(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, 
 
 int cnn_col2im_relu(const float *dcols, const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho,
                     int Wo, int Kp, __nv_bfloat16 *dz, cudaStream_t st) {
-    col2im_relu_kernel<<<grid_for((int64_t)Nb * H * W * C), 256, 0, st>>>(dcols, x, Nb, H, W, C, stride, Ho, Wo, Kp,
-                                                                         dz);
+    const int64_t total = (int64_t)Nb * H * W * C;
+    const bool aligned = (reinterpret_cast<uintptr_t>(dcols) & 15) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0 &&
+                         (reinterpret_cast<uintptr_t>(dz) & 15) == 0;
+    if (aligned && C % 8 == 0 && Kp % 4 == 0 && total < ((int64_t)1 << 31) &&
+        (int64_t)Nb * Ho * Wo * Kp < ((int64_t)1 << 31))
+        col2im_relu_vec_kernel<<<grid_for(total / 8), 256, 0, st>>>(dcols, x, H, W, C, stride, Ho, Wo, Kp,
+                                                                     (uint32_t)(total / 8), dz);
+    else
+        col2im_relu_kernel<<<grid_for(total), 256, 0, st>>>(dcols, x, Nb, H, W, C, stride, Ho, Wo, Kp, dz);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
@@ -588,9 +659,13 @@ int cnn_head_back(const float *feat, const float *dl, int Nb, int C, const float
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
-int cnn_bias_grad(const __nv_bfloat16 *dz, int64_t P, int C, float *db, cudaStream_t st) {
-    bias_grad_kernel<<<C, 256, 0, st>>>(dz, P, C, db);
-    note_launch();
+int cnn_bias_grad(const __nv_bfloat16 *dz, int64_t P, int C, float *db, float *part, cudaStream_t st) {
+    if (C < 1 || C > 256 || 256 % C || P < 1) return SP_EINVAL;
+    const int nchunk = (int)std::min<int64_t>(kBiasChunks, (P + 255) / 256);
+    const int64_t rows = (P + nchunk - 1) / nchunk;
+    bias_grad_part_kernel<<<nchunk, 256, 0, st>>>(dz, P, C, rows, part);
+    bias_grad_sum_kernel<<<(C + 255) / 256, 256, 0, st>>>(part, nchunk, C, db);
+    note_launch(2);
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

@@ -29,7 +29,10 @@ int cnn_fuse_loss(const float *l1, const float *l2, const float *label, int Nb, 
                   float *loss, cudaStream_t st);
 int cnn_head_back(const float *feat, const float *dl, int Nb, int C, const float *w, float *dfeat, float *dw,
                   float *db, cudaStream_t st);
-int cnn_bias_grad(const __nv_bfloat16 *dz, int64_t P, int C, float *db, cudaStream_t st);
+// db[c] += sum_p dz[p][c] (C divides 256); part: kBiasChunks * C floats of
+// workspace (deterministic two-stage sum).
+constexpr int kBiasChunks = 512;
+int cnn_bias_grad(const __nv_bfloat16 *dz, int64_t P, int C, float *db, float *part, cudaStream_t st);
 int cnn_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
              int64_t step, __nv_bfloat16 *wb, cudaStream_t st);
 int cnn_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b, cudaStream_t st);

@@ -193,6 +193,29 @@ int alloc_host(void **p, int64_t bytes) {
     return SP_OK;
 }
 
+// Releases the classifier stage of sp_stream_attach (also after a failed
+// attach, which leaves the stream as it was).
+void cls_free(sp_stream *s) {
+    for (size_t i = 0; s->recs && i < s->slots.size(); ++i) {
+        JobRec &j = s->recs[i];
+        cudaFreeHost(j.h_kept);
+        cudaFreeHost(j.h_prob);
+        if (j.done) cudaEventDestroy(j.done);
+    }
+    s->recs.reset();
+    s->free_recs.clear();
+    if (s->cls_stream) cudaStreamDestroy(s->cls_stream);
+    for (void *q : {(void *)s->d_kept, (void *)s->d_sub, s->d_ft, s->d_img, s->d_work, (void *)s->d_shift,
+                    (void *)s->d_prob})
+        cudaFree(q);
+    s->cls_stream = nullptr;
+    s->d_kept = nullptr;
+    s->d_sub = nullptr;
+    s->d_ft = s->d_img = s->d_work = nullptr;
+    s->d_shift = nullptr;
+    s->d_prob = nullptr;
+}
+
 void stream_free(sp_stream *s) {
     for (int i = 0; i < kMaxStreams; ++i) {
         Launch &l = s->launches[i];
@@ -214,24 +237,11 @@ void stream_free(sp_stream *s) {
         cudaFreeHost(sl.h_cands);
         cudaFreeHost(sl.h_count);
     }
-    for (size_t i = 0; s->recs && i < s->slots.size(); ++i) {
-        JobRec &j = s->recs[i];
-        cudaFreeHost(j.h_kept);
-        cudaFreeHost(j.h_prob);
-        if (j.done) cudaEventDestroy(j.done);
-    }
     for (cudaEvent_t e : s->staged_ev)
         if (e) cudaEventDestroy(e);
     cudaFree(s->d_rings);
     if (s->search_stream) cudaStreamDestroy(s->search_stream);
-    if (s->cls_stream) cudaStreamDestroy(s->cls_stream);
-    cudaFree(s->d_kept);
-    cudaFree(s->d_sub);
-    cudaFree(s->d_ft);
-    cudaFree(s->d_img);
-    cudaFree(s->d_work);
-    cudaFree(s->d_shift);
-    cudaFree(s->d_prob);
+    cls_free(s);
 }
 
 int64_t slot_bytes(const sp_stream *s) {
@@ -800,6 +810,7 @@ extern "C" int sp_stream_attach(sp_stream *s, const sp_sift_params *params, sp_c
     s->sift_buf.assign((size_t)kept_cap, sp_cand{});
     if (clf) {
         const int64_t nimg = (int64_t)kClsCap * 256 * 256;
+        const int64_t bytes0 = s->device_bytes;
         s->work_bytes = sp_cnn_features_workspace_bytes(kClsCap);
         rc = alloc_dev((void **)&s->d_kept, (int64_t)kClsCap * (int64_t)sizeof(sp_cand), &s->device_bytes);
         if (!rc) rc = alloc_dev((void **)&s->d_sub, (int64_t)kClsCap * 256 * t_in * 4, &s->device_bytes);
@@ -835,7 +846,11 @@ extern "C" int sp_stream_attach(sp_stream *s, const sp_sift_params *params, sp_c
             cudaGetLastError();
             rc = SP_ECUDA;
         }
-        if (rc) return rc;  // what was allocated is freed by sp_stream_destroy
+        if (rc) {
+            cls_free(s);
+            s->device_bytes = bytes0;
+            return rc;
+        }
     }
     s->sift = *params;
     s->clf = clf;

@@ -146,3 +146,12 @@ def test_stream_argument_checks(lib):
     t0 = lib.sp_stream_now()
     t1 = lib.sp_stream_now()
     assert t1 >= t0 > 0
+
+
+def test_launch_counter_needs_no_device(lib):
+    """The launch counter is host state, readable without a GPU; a call
+    rejected by its argument checks launches nothing."""
+    c0 = sp.launch_count()
+    assert c0 >= 0
+    assert lib.sp_single_pulse_search(None, 0, 0, None, 0, 6.0, 0, None, 0, None, 0, None, None) == sp.SP_EINVAL
+    assert sp.launch_count() == c0

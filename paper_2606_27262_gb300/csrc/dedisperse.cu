@@ -163,7 +163,7 @@ __device__ __forceinline__ void add_quad(uint32_t wa, uint32_t wb, uint32_t wc, 
 // a persistent CTA keeps using its mbarriers: chunk g lives in raw slot
 // g % NS and completes phase (g / NS) & 1 of that slot's barrier.
 //
-// Iteration k: warp 0 issues chunk k+2; every warp sums chunk k from copies
+// Iteration k: warp (k+2) % CH issues chunk k+2; every warp sums chunk k from copies
 // buffer k & 1, then waits for chunk k+1's bytes and expands its channel of
 // it into copies buffer (k+1) & 1; barrier.  A raw slot is refilled two
 // barriers after its chunk was expanded; a copies buffer one barrier after
@@ -273,10 +273,14 @@ __device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const 
             }
         }
     };
-    int4 g_next = zero4;  // warp 0: geometry of the next chunk to issue
+    // Warp 0 issues chunks 0 and 1; chunk j >= 2 is issued by warp j % CH,
+    // so that the issuing work (and the wait at the next barrier for the
+    // warp doing it) rotates over the warps.  Each warp holds the geometry of
+    // the next chunk it will issue, loaded CH chunks ahead.
+    const int first_mine = warp >= 2 ? warp : warp + CH;
+    int4 g_mine = load_geo(first_mine);
     if (warp == 0) {
         const int4 g0 = load_geo(0), g1 = load_geo(1);
-        g_next = load_geo(2);
         issue(0, g0);
         if (nchunks > 1) issue(1, g1);
     }
@@ -308,9 +312,9 @@ __device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const 
         const int nc = min(CH, nchan - k * CH);
         if (!failed && k + 2 < nchunks) {
             last_issued = k + 2;
-            if (warp == 0) {
-                issue(k + 2, g_next);
-                g_next = load_geo(k + 3);
+            if (warp == (k + 2) % CH) {
+                issue(k + 2, g_mine);
+                g_mine = load_geo(k + 2 + CH);
             }
         }
         if (warp_active && !failed) {

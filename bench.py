@@ -95,7 +95,7 @@ def parse_args(argv=None):
     p.add_argument("--dmt-budget-gb", type=float, default=24.0,
                    help="batched workload: DM-transform bytes per group arena (GB)")
     p.add_argument("--no-per-beam", action="store_true", help="batched workload: skip the comparisons")
-    p.add_argument("--batch-mode", choices=["persistent", "grid"], default="grid",
+    p.add_argument("--batch-mode", choices=["persistent", "grid"], default="persistent",
                    help="batched workload: dedispersion launch style of the timed step (grid: one CTA per "
                         "work item; persistent: a resident grid draining a work queue)")
     return p.parse_args(argv)

@@ -65,8 +65,9 @@ const char *sp_strerror(int code);
 
 /* Kernel launches the library has issued in this process, for measurement
  * (no counterpart in the paper): every kernel a call launches counts once;
- * kernels recorded into a CUDA graph (sp_batch_capture) count once per
- * replay (sp_batch_launch), not at capture.  Never fails. */
+ * kernels that sp_batch_capture records count once per sp_batch_launch, not
+ * at capture.  (A graph the caller captures around library calls counts its
+ * kernels once, when they are recorded.)  Never fails. */
 uint64_t sp_launch_count(void);
 
 /* ------------------------------------------------------------------ plan --

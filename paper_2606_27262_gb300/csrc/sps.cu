@@ -66,11 +66,11 @@ __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restric
         s2 += x * x;
     }
     const int4 *vrow = reinterpret_cast<const int4 *>(row + head);
-    for (int64_t i = threadIdx.x; i < nvec; i += 256) {
+#pragma unroll 4
+    for (int64_t i = threadIdx.x; i < nvec; i += 256) {  // four 16-byte loads in flight per thread
         const int4 q = __ldg(vrow + i);
-        const int64_t a = q.x, bb = q.y, c = q.z, e = q.w;
-        s1 += a + bb + c + e;
-        s2 += a * a + bb * bb + c * c + e * e;
+        s1 += (int64_t)q.x + q.y + (int64_t)q.z + q.w;
+        s2 += (int64_t)q.x * q.x + (int64_t)q.y * q.y + (int64_t)q.z * q.z + (int64_t)q.w * q.w;
     }
     for (int64_t t = head + 4 * nvec + threadIdx.x; t < hi; t += 256) {
         const int64_t x = __ldg(row + t);
@@ -84,6 +84,8 @@ __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restric
         red2[threadIdx.x >> 5] = s2;
     }
     __syncthreads();
+    __shared__ double s_frac, s_inv_sigma;
+    const int64_t idx = d * nblk + b;
     if (threadIdx.x == 0) {
         int64_t S1 = 0, S2 = 0;
         for (int i = 0; i < 8; ++i) {
@@ -93,16 +95,17 @@ __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restric
         const int64_t n = hi - lo;
         int64_t m0 = S1 / n;
         if (S1 - m0 * n < 0) --m0;  // floor for negative sums
-        const double frac = (double)(S1 - m0 * n) / (double)n;
+        s_frac = (double)(S1 - m0 * n) / (double)n;
         const __int128 var_n2 = (__int128)n * S2 - (__int128)S1 * S1;
-        const double inv_sigma = var_n2 > 0 ? (double)n / sqrt((double)var_n2) : 0.0;
-        const int64_t idx = d * nblk + b;
+        s_inv_sigma = var_n2 > 0 ? (double)n / sqrt((double)var_n2) : 0.0;
         m0_out[idx] = (int32_t)m0;
-        for (int k = 0; k < wl.nw; ++k) {
-            const double w = (double)wl.w[k];
-            const double inv = inv_sigma / sqrt(w);
-            coef_out[idx * wl.nw + k] = make_float2((float)inv, (float)(w * frac * inv));
-        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < wl.nw) {  // one width per thread
+        const int k = threadIdx.x;
+        const double w = (double)wl.w[k];
+        const double inv = s_inv_sigma / sqrt(w);
+        coef_out[idx * wl.nw + k] = make_float2((float)inv, (float)(w * s_frac * inv));
     }
 }
 

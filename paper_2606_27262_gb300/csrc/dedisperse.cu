@@ -179,7 +179,7 @@ struct Shape {
     static constexpr int GROUP = kDedispTileGroupDms / DT;  // DM tiles per raster group
     static_assert(NDT == 4, "offset table is read as int4 per thread");
     static_assert(SPT % 4 == 0 && T <= kDedispMaxTimeTile, "time tile");
-    static_assert(CH <= kDedispMaxChanChunk && CH % 4 == 0, "warp 0 lanes issue one channel each; quads");
+    static_assert(CH <= kDedispMaxChanChunk && CH % 4 == 0, "the issuing warp's lanes copy one channel each; quads");
     static_assert(8 * NS <= kDedispItemOffset && kDedispItemOffset + 8 <= kDedispGeoOffset,
                   "mbarriers, work item and geometry ring overlap");
     static_assert(kDedispGeoOffset + NS * CH * 16 <= kDedispOffTabOffset, "geometry ring overlaps the offsets");
@@ -223,7 +223,7 @@ __device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const 
 
     auto slot_of = [&](int kk) { return (int)((seq0 + (uint32_t)kk) % NS); };
     auto parity_of = [&](int kk) { return ((seq0 + (uint32_t)kk) / NS) & 1u; };
-    auto issue = [&](int kk, int4 g) {  // warp 0; chunk kk into its raw slot
+    auto issue = [&](int kk, int4 g) {  // by one warp: chunk kk into its raw slot
         const int sl = slot_of(kk);
         const int nc = min(CH, nchan - kk * CH);
         uint32_t bytes = (lane < nc) ? (uint32_t)g.y + 16u : 0u;

@@ -66,3 +66,24 @@ def test_profiled_traffic_guard(tmp_path, monkeypatch):
                                      '"dram_bytes_per_launch_full_config": 5}' % h)
     assert bench.profiled_traffic(131072) == 5.0
     assert bench.profiled_traffic(16384) is None  # another workload length
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the CPU oracle on the host cores) prints
+    one JSON line with the contract's keys; small workload, one step."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--n-out", "16384",
+                          "--steps", "1", "--warmup", "0", "--cpu-stride", "256"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}

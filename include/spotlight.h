@@ -141,6 +141,20 @@ int sp_dedisp_shape_info(int32_t shape, int32_t *dm_tile, int32_t *time_tile, in
 int sp_plan_create_shaped(const double *freqs_mhz, int32_t nchan, double tsamp_s,
                           const double *dms, int32_t ndm, int32_t shape, sp_plan **out);
 int sp_plan_shape(const sp_plan *plan, int32_t *shape, int32_t *ntiles, int32_t *smem_bytes);
+/* Host-only check of a plan's staging tables (no counterpart in the paper;
+ * no device is touched): builds the plan of (freqs, tsamp, dms, shape) on
+ * the host and checks, for a beam of n_out searched samples, every access
+ * the dedispersion kernel makes with its tables -- 16-byte alignment and
+ * bounds of the bulk copies (inside the staged row of pitch
+ * sp_staged_pitch(n_out + max_delay) and inside the raw slot), the four
+ * shifted copies inside the copies buffer, and every shared load of the
+ * sums inside its channel's copy.  h_report [8] (host): DM tiles, channel
+ * chunks, copies bytes, raw bytes, dynamic shared memory bytes of the
+ * kernel, number of violated conditions (0 for a sound plan), max delay,
+ * staged pitch.  Errors: SP_EINVAL (the sp_plan_create argument checks,
+ * shape, n_out < 1, h_report NULL). */
+int sp_plan_check_tables(const double *freqs_mhz, int32_t nchan, double tsamp_s, const double *dms,
+                         int32_t ndm, int32_t shape, int64_t n_out, int64_t *h_report);
 int sp_autotune_dedisperse(const double *freqs_mhz, int32_t nchan, double tsamp_s,
                            const double *dms, int32_t ndm, int64_t n_out_sample, int32_t reps,
                            float *h_ms, int32_t *best, void *stream);

@@ -100,6 +100,7 @@ SIGNATURES = {
     "sp_stream_now": (F64, []),
     "sp_stream_attach": (ctypes.c_int, [P, P, P, I32, I32]),
     "sp_launch_count": (ctypes.c_uint64, []),
+    "sp_plan_check_tables": (ctypes.c_int, [P, I32, F64, P, I32, I32, I64, P]),
     "sp_stream_poll_sifted": (ctypes.c_int, [P, I32, P, P, P, P, I32, P]),
     "sp_sift": (ctypes.c_int, [P, I64, P, I32, P, I32, F64, P, P, I64, P, P]),
     "sp_inject_quantised": (ctypes.c_int, [P, P, I64, I32, F64, F64, F64, P]),
@@ -532,6 +533,18 @@ class GulpResult(ctypes.Structure):
                 ("t0", ctypes.c_int64), ("count", ctypes.c_int64), ("t_push", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("t_search", ctypes.c_double), ("kept", ctypes.c_int64),
                 ("accepted", ctypes.c_int64)]
+
+
+def plan_check_tables(freqs_mhz, tsamp_s: float, dms, shape: int, n_out: int) -> dict:
+    """Host-only check of a plan's staging tables against the dedispersion
+    kernel's accesses (sp_plan_check_tables); no GPU needed."""
+    f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+    d = np.ascontiguousarray(dms, dtype=np.float64)
+    rep = np.zeros(8, np.int64)
+    _check(_lib().sp_plan_check_tables(f.ctypes.data, f.size, float(tsamp_s), d.ctypes.data, d.size, int(shape),
+                                       int(n_out), rep.ctypes.data), "sp_plan_check_tables")
+    keys = ("ntiles", "nchunks", "copies_bytes", "raw_bytes", "smem_bytes", "violations", "max_delay", "pitch")
+    return dict(zip(keys, (int(v) for v in rep)))
 
 
 def launch_count() -> int:

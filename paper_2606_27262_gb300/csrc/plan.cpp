@@ -125,18 +125,13 @@ static int upload(T **dst, const T *src, size_t n) {
     return SP_OK;
 }
 
-static int create_plan(const double *freqs_mhz, int32_t nchan, double tsamp_s, const double *dms, int32_t ndm,
-                       int32_t shape, sp_plan **out) {
-    if (!out) return SP_EINVAL;
-    *out = nullptr;
+// The host half of a plan: delays, DM tiles, staging tables and the
+// kernel's shared-memory size; no device memory.
+static int build_host_plan(const double *freqs_mhz, int32_t nchan, double tsamp_s, const double *dms, int32_t ndm,
+                           int32_t shape, sp_plan *p, std::vector<int32_t> &geo, std::vector<int32_t> &off) {
     if (shape < 0 || shape >= kDedispNumShapes) return SP_EINVAL;
-    sp_plan *p = new (std::nothrow) sp_plan();
-    if (!p) return SP_ENOMEM;
     int rc = compute_delays(freqs_mhz, nchan, tsamp_s, dms, ndm, p->delays, &p->max_delay);
-    if (rc) {
-        delete p;
-        return rc;
-    }
+    if (rc) return rc;
     p->nchan = nchan;
     p->ndm = ndm;
     p->tsamp = tsamp_s;
@@ -178,9 +173,24 @@ static int create_plan(const double *freqs_mhz, int32_t nchan, double tsamp_s, c
     }
     p->ntiles = (int32_t)p->tile_first.size();
     p->nchunks = (nchan + p->chan_chunk - 1) / p->chan_chunk;
-    std::vector<int32_t> geo, off;
     build_chunk_tables(*p, geo, off, &p->copies_max, &p->raw_max);
     p->smem_bytes = dedisp_header_bytes(p->chan_chunk, p->dm_tile) + kDedispRawSlots * p->raw_max + 2 * p->copies_max;
+    return SP_OK;
+}
+
+static int create_plan(const double *freqs_mhz, int32_t nchan, double tsamp_s, const double *dms, int32_t ndm,
+                       int32_t shape, sp_plan **out) {
+    if (!out) return SP_EINVAL;
+    *out = nullptr;
+    if (shape < 0 || shape >= kDedispNumShapes) return SP_EINVAL;
+    sp_plan *p = new (std::nothrow) sp_plan();
+    if (!p) return SP_ENOMEM;
+    std::vector<int32_t> geo, off;
+    int rc = build_host_plan(freqs_mhz, nchan, tsamp_s, dms, ndm, shape, p, geo, off);
+    if (rc) {
+        delete p;
+        return rc;
+    }
 
     int smem_optin = 0;
     if (cudaGetDevice(&p->device) != cudaSuccess ||
@@ -280,5 +290,57 @@ extern "C" int sp_plan_status(const sp_plan *p, int32_t *h_status, int32_t clear
 extern "C" int sp_plan_delays(const sp_plan *p, int32_t *h_out) {
     if (!p || !h_out) return SP_EINVAL;
     std::memcpy(h_out, p->delays.data(), p->delays.size() * sizeof(int32_t));
+    return SP_OK;
+}
+
+// Host-side check of the staging tables against every access the
+// dedispersion kernel makes with them (see dedisperse.cu): bulk copies of
+// raw windows (16-byte aligned, inside the staged row and the raw slot),
+// the four shifted copies (inside the copies buffer, rows 16-byte aligned),
+// and every shared load of the sums (inside the channel's copy, within the
+// R + 16 bytes its copy was built from).
+extern "C" int sp_plan_check_tables(const double *freqs_mhz, int32_t nchan, double tsamp_s, const double *dms,
+                                    int32_t ndm, int32_t shape, int64_t n_out, int64_t *h_report) {
+    if (!h_report || n_out <= 0) return SP_EINVAL;
+    sp_plan p;
+    std::vector<int32_t> geo, off;
+    int rc = build_host_plan(freqs_mhz, nchan, tsamp_s, dms, ndm, shape, &p, geo, off);
+    if (rc) return rc;
+    const int32_t CH = p.chan_chunk, DT = p.dm_tile, T = p.time_tile;
+    const int64_t n_in = n_out + p.max_delay;
+    const int64_t pitch = dedisp_pitch(n_in);
+    const int64_t ntime = (n_out + T - 1) / T;
+    int64_t bad = 0;
+    for (int32_t j = 0; j < p.ntiles; ++j) {
+        for (int32_t k = 0; k < p.nchunks; ++k) {
+            const int32_t nc = std::min(CH, p.nchan - k * CH);
+            for (int32_t i = 0; i < nc; ++i) {
+                const int32_t *g = &geo[(((size_t)j * p.nchunks + k) * CH + i) * 4];
+                const int32_t rel = g[0], R = g[1], soff = g[2], roff = g[3];
+                bad += (rel < 0) + (rel % 16 != 0) + (R % 16 != 0) + (R < T) + (soff % 16 != 0) + (roff % 16 != 0);
+                bad += (roff + R + 16 > p.raw_max) + (soff + 4 * R > p.copies_max);
+                // the last time tile's window must end inside the staged row
+                bad += ((ntime - 1) * T + rel + R + 16 > pitch);
+                const int32_t *o = &off[(((size_t)j * p.nchunks + k) * CH + i) * DT];
+                for (int32_t dl = 0; dl < DT; ++dl) {
+                    const int32_t dd = std::min(dl, p.tile_count[j] - 1);
+                    const int32_t shift = p.delays[(size_t)(p.tile_first[j] + dd) * p.nchan + k * CH + i] - rel;
+                    const int32_t r = shift & 3, w0 = shift & ~3;
+                    bad += (shift < 0) + (o[dl] != soff + r * R + w0);
+                    // words w0/4 .. (w0 + T)/4 - 1 of copy r: inside the copy
+                    // and built from bytes below R + 16 of the raw window
+                    bad += (w0 + T > R) + (w0 + T + r > R + 16);
+                }
+            }
+        }
+    }
+    h_report[0] = p.ntiles;
+    h_report[1] = p.nchunks;
+    h_report[2] = p.copies_max;
+    h_report[3] = p.raw_max;
+    h_report[4] = p.smem_bytes;
+    h_report[5] = bad;
+    h_report[6] = p.max_delay;
+    h_report[7] = pitch;
     return SP_OK;
 }

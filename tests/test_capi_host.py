@@ -155,3 +155,31 @@ def test_launch_counter_needs_no_device(lib):
     assert c0 >= 0
     assert lib.sp_single_pulse_search(None, 0, 0, None, 0, 6.0, 0, None, 0, None, 0, None, None) == sp.SP_EINVAL
     assert sp.launch_count() == c0
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_staging_tables_sound_for_every_workload(lib, shape):
+    """Every bulk copy, shifted copy and shared load the dedispersion kernel
+    makes with a plan's tables stays aligned and in bounds (host-only check),
+    and the kernel's shared memory fits a GB300 SM: configs 1 and 2, the
+    three DM plans of config 3 at both ends of its length range, and random
+    unsorted DM lists with duplicates over ragged channel counts."""
+    cases = []
+    c1, c2 = synth.config1(), synth.config2()
+    cases.append((c1.freqs, c1.tsamp, c1.dms, c1.n_out))
+    cases.append((c2.freqs, c2.tsamp, c2.dms, c2.n_out))
+    f4k = synth.band_freqs(4096)
+    for dm_max in (500.0, 1000.0, 2000.0):
+        dms = synth.dm_plan_upto(dm_max)
+        for n_out in (16384, 131072):
+            cases.append((f4k, synth.TSAMP, dms, n_out))
+    rng = np.random.default_rng(5)
+    for nchan in (1, 7, 64, 100, 256):
+        dms = rng.choice(np.arange(0, 800.0, 0.5), size=int(rng.integers(1, 300)))
+        cases.append((synth.band_freqs(nchan), synth.TSAMP, dms, int(rng.integers(1, 5000))))
+    for freqs, tsamp, dms, n_out in cases:
+        rep = sp.plan_check_tables(freqs, tsamp, dms, shape, n_out)
+        assert rep["violations"] == 0, rep
+        assert rep["smem_bytes"] <= 227 * 1024, rep
+    with pytest.raises(sp.SpotlightError):
+        sp.plan_check_tables(c1.freqs, c1.tsamp, c1.dms, 7, 100)  # no such shape

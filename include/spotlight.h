@@ -43,6 +43,7 @@ extern "C" {
 #define SP_ENOMEM (-5)     /* device or host allocation failed                */
 #define SP_EWORKSPACE (-6) /* workspace pointer null or too small             */
 #define SP_ELIMIT (-7)     /* a size is beyond a documented library limit     */
+#define SP_ETIMEOUT (-8)   /* a kernel gave up a bounded wait: outputs void   */
 
 /* Library limits. */
 #define SP_MAX_WIDTHS 16        /* trial boxcar widths per search           */
@@ -92,7 +93,11 @@ int sp_plan_destroy(sp_plan *plan);
  * be NULL. */
 int sp_plan_info(const sp_plan *plan, int32_t *max_delay, int32_t *nchan, int32_t *ndm);
 /* Device status word of the plan's kernels: 0, or SP_STATUS_* bits set by
- * a kernel that gave up a bounded wait (its outputs are then invalid).
+ * a kernel that gave up a bounded wait.  A set bit voids every output of
+ * every launch that flagged it since the last clear -- the whole DM
+ * transform, and for a batched launch every beam of the batch, not only the
+ * tile whose wait ran out: a CTA that gives up twice may leave copies in
+ * flight that land in shared memory a later CTA of the same launch uses.
  * Reads it after synchronising the device; clear != 0 resets it. */
 #define SP_STATUS_STAGING_TIMEOUT 1
 int sp_plan_status(const sp_plan *plan, int32_t *h_status, int32_t clear);
@@ -213,7 +218,7 @@ int sp_dedisperse_staged(const sp_plan *plan, const uint8_t *d_staged, int64_t p
  *     `stream`, so this call cannot be captured into a CUDA graph; the batch
  *     object below can).
  * A staging wait that runs out sets SP_STATUS_STAGING_TIMEOUT in the status
- * word of h_beams[0].plan.
+ * word of h_beams[0].plan; it voids the outputs of every beam of the call.
  * Errors: SP_EINVAL, SP_ESHAPE, SP_EWORKSPACE, SP_ELIMIT, SP_ECUDA. */
 typedef struct {
     const sp_plan *plan;
@@ -274,7 +279,9 @@ int sp_single_pulse_search(const int32_t *d_dmt, int32_t ndm, int64_t n_out,
  * 5751 DMs x 131072 samples / 8192-sample blocks x 9 widths, needs 8.7 MB)
  * return SP_ELIMIT.  The call allocates nothing: no cudaMalloc, no cudaFree.
  * The first call on a device looks up the array's device address with that
- * device current (make that first call before any stream capture).  Every
+ * device current (make that first call before any stream capture) and keeps
+ * it for the life of the process; it does not survive cudaDeviceReset, so do
+ * not call this entry point on a device after resetting it.  Every
  * call on a device shares the one array and it keeps the last call's
  * contents (each call overwrites what it reads); calls whose GPU work
  * overlaps -- on different streams or different host threads -- race on it
@@ -608,7 +615,10 @@ int sp_cnn_extract(const sp_plan *plan, const uint8_t *d_staged, int64_t pitch, 
  *   (-1 without a classifier); either may be NULL.  Result fields: kept =
  *   total peaks the sifter kept (status SP_EOVERFLOW when above kept_cap);
  *   accepted = how many of the returned ones have p >= 0.5 (all of them
- *   without a classifier). */
+ *   without a classifier).
+ * Every batch has its own status word: if a bounded wait of its
+ *   dedispersion ran out, each gulp of that batch is returned with status
+ *   SP_ETIMEOUT, count 0 and no candidates (its outputs are void). */
 typedef struct sp_stream sp_stream;
 typedef struct {
     int32_t beam;

@@ -70,7 +70,7 @@ def _bind(lib):
     lib.oracle_dedisperse.restype = ctypes.c_int
     lib.oracle_nblocks.argtypes = [i64, i64]
     lib.oracle_nblocks.restype = i64
-    lib.oracle_moments.argtypes = [P, i32, i64, i64, P, P, P]
+    lib.oracle_moments.argtypes = [P, i32, i64, i64, P, P, P, P]
     lib.oracle_moments.restype = ctypes.c_int
     lib.oracle_boxcar_snr.argtypes = [P, i32, i64, P, i32, i64, P]
     lib.oracle_boxcar_snr.restype = ctypes.c_int
@@ -135,16 +135,22 @@ def nblocks(n_out: int, norm_block: int, lib=None) -> int:
 
 
 def moments(dmt: np.ndarray, norm_block: int, lib=None):
-    """(count, sum, sum of squares), each int64 [nrows][nblk]."""
+    """(count, sum, sum of squares) [nrows][nblk]: count and sum int64, the
+    sum of squares exact Python integers (object array; it is formed in 128
+    bits because it can exceed 2^63)."""
     lib = lib or load()
     a = np.ascontiguousarray(dmt, dtype=np.int32)
     nb = nblocks(a.shape[1], norm_block, lib)
     cnt = np.empty((a.shape[0], nb), np.int64)
     sx = np.empty_like(cnt)
-    sxx = np.empty_like(cnt)
-    rc = lib.oracle_moments(_p(a), a.shape[0], a.shape[1], int(norm_block), _p(cnt), _p(sx), _p(sxx))
+    hi = np.empty_like(cnt)
+    lo = np.empty((a.shape[0], nb), np.uint64)
+    rc = lib.oracle_moments(_p(a), a.shape[0], a.shape[1], int(norm_block), _p(cnt), _p(sx), _p(hi), _p(lo))
     if rc != 0:
         raise ValueError("oracle_moments failed")
+    sxx = np.empty((a.shape[0], nb), dtype=object)
+    for idx in np.ndindex(sxx.shape):
+        sxx[idx] = (int(hi[idx]) << 64) + int(lo[idx])
     return cnt, sx, sxx
 
 

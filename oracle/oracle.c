@@ -14,7 +14,9 @@
  *                         shift every channel by its delay and sum -> the
  *                         "DM transform" (one time series per trial DM).
  *   oracle_moments     -- Sec. 3.1.2 normalisation: per-row, per-block count,
- *                         sum and sum of squares (exact, 64-bit).
+ *                         sum (exact, 64-bit) and sum of squares (exact,
+ *                         128-bit: a block of int32 values near 2^31 has a
+ *                         sum of squares far beyond 2^63).
  *   oracle_boxcar_snr  -- Sec. 3.1.2 matched filter: boxcar of width w as a
  *                         difference of the running cumulative sum, S/N =
  *                         (S - w*mean) / (sigma*sqrt(w)).
@@ -136,9 +138,23 @@ static int64_t block_end(int64_t b, int64_t norm_block, int64_t nblk, int64_t n_
 }
 
 /* Per row r and block b: count, sum and sum of squares of the DM-transform
- * samples in the block.  Arrays are [nrows][nblk]. */
+ * samples in the block.  Arrays are [nrows][nblk].  The sum of squares is
+ * formed in 128 bits and returned as its high (signed) and low (unsigned)
+ * 64-bit halves. */
+static void block_moments(const int32_t *row, int64_t lo, int64_t hi, int64_t *s1_out, __int128 *s2_out)
+{
+    int64_t s1 = 0;
+    __int128 s2 = 0;
+    for (int64_t t = lo; t < hi; ++t) {
+        s1 += row[t];
+        s2 += (__int128)((int64_t)row[t] * row[t]);
+    }
+    *s1_out = s1;
+    *s2_out = s2;
+}
+
 int oracle_moments(const int32_t *dmt, int32_t nrows, int64_t n_out,
-                   int64_t norm_block, int64_t *cnt, int64_t *sx, int64_t *sxx)
+                   int64_t norm_block, int64_t *cnt, int64_t *sx, int64_t *sxx_hi, uint64_t *sxx_lo)
 {
     if (nrows <= 0 || n_out <= 0)
         return -1;
@@ -146,16 +162,15 @@ int oracle_moments(const int32_t *dmt, int32_t nrows, int64_t n_out,
     for (int32_t r = 0; r < nrows; ++r) {
         const int32_t *row = dmt + (int64_t)r * n_out;
         for (int64_t b = 0; b < nblk; ++b) {
-            int64_t s1 = 0, s2 = 0;
             const int64_t lo = block_start(b, norm_block, nblk);
             const int64_t hi = block_end(b, norm_block, nblk, n_out);
-            for (int64_t t = lo; t < hi; ++t) {
-                s1 += row[t];
-                s2 += (int64_t)row[t] * row[t];
-            }
+            int64_t s1;
+            __int128 s2;
+            block_moments(row, lo, hi, &s1, &s2);
             cnt[(int64_t)r * nblk + b] = hi - lo;
             sx[(int64_t)r * nblk + b] = s1;
-            sxx[(int64_t)r * nblk + b] = s2;
+            sxx_hi[(int64_t)r * nblk + b] = (int64_t)(s2 >> 64);
+            sxx_lo[(int64_t)r * nblk + b] = (uint64_t)s2;
         }
     }
     return 0;
@@ -179,12 +194,19 @@ int oracle_boxcar_snr(const int32_t *dmt, int32_t nrows, int64_t n_out,
     const int64_t nblk = oracle_nblocks(n_out, norm_block);
     int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * nblk * nrows);
     int64_t *sx = (int64_t *)malloc(sizeof(int64_t) * nblk * nrows);
-    int64_t *sxx = (int64_t *)malloc(sizeof(int64_t) * nblk * nrows);
+    __int128 *sxx = (__int128 *)malloc(sizeof(__int128) * nblk * nrows);
     if (!cnt || !sx || !sxx) {
         free(cnt); free(sx); free(sxx);
         return -2;
     }
-    oracle_moments(dmt, nrows, n_out, norm_block, cnt, sx, sxx);
+    for (int32_t r = 0; r < nrows; ++r)
+        for (int64_t b = 0; b < nblk; ++b) {
+            const int64_t lo = block_start(b, norm_block, nblk);
+            const int64_t hi = block_end(b, norm_block, nblk, n_out);
+            cnt[(int64_t)r * nblk + b] = hi - lo;
+            block_moments(dmt + (int64_t)r * n_out, lo, hi, &sx[(int64_t)r * nblk + b],
+                          &sxx[(int64_t)r * nblk + b]);
+        }
 
     int rc = 0;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -211,7 +233,7 @@ int oracle_boxcar_snr(const int32_t *dmt, int32_t nrows, int64_t n_out,
                     b = nblk - 1;
                 const int64_t n = cnt[(int64_t)r * nblk + b];
                 const int64_t s1 = sx[(int64_t)r * nblk + b];
-                const int64_t s2 = sxx[(int64_t)r * nblk + b];
+                const __int128 s2 = sxx[(int64_t)r * nblk + b];
                 const __int128 var_n2 = (__int128)n * s2 - (__int128)s1 * s1;
                 const int64_t S = cum[t + w] - cum[t];
                 const __int128 num = (__int128)n * S - (__int128)w * s1;

@@ -33,6 +33,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libspotlight.so")
 
 SP_OK, SP_EINVAL, SP_ESHAPE, SP_ECUDA, SP_EOVERFLOW, SP_ENOMEM, SP_EWORKSPACE, SP_ELIMIT = 0, -1, -2, -3, -4, -5, -6, -7
+SP_ETIMEOUT = -8
 SP_MAX_WIDTHS = 16
 SP_MAX_WIDTH = 1024
 

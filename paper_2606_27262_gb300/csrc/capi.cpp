@@ -91,6 +91,7 @@ extern "C" const char *sp_strerror(int code) {
         case SP_ENOMEM: return "allocation failed";
         case SP_EWORKSPACE: return "workspace missing, misaligned or too small";
         case SP_ELIMIT: return "size beyond a library limit";
+        case SP_ETIMEOUT: return "a bounded wait in a kernel ran out; its outputs are void";
         default: return "unknown error";
     }
 }

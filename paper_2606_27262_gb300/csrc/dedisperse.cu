@@ -570,7 +570,7 @@ int64_t dedisp_time_tiles(const sp_plan *plan, int64_t n_out) {
 int dedisp_configure(const sp_plan *plan) { return configure_shape(plan->shape, plan->smem_bytes); }
 
 int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, int64_t n_out, int32_t *d_out,
-                      cudaStream_t stream) {
+                      cudaStream_t stream, int32_t *status) {
     int rc = dedisp_configure(plan);
     if (rc) return rc;
     const ShapeKernels &k = kShapes[plan->shape];
@@ -578,7 +578,8 @@ int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, i
     k.grid<<<grid, k.threads, plan->smem_bytes, stream>>>(d_xt, pitch, plan->nchan, plan->nchunks,
                                                           plan->d_tile_first, plan->d_tile_count,
                                                           plan->d_chunk_geo, plan->d_chunk_off, plan->copies_max,
-                                                          plan->raw_max, n_out, d_out, plan->d_status);
+                                                          plan->raw_max, n_out, d_out,
+                                                          status ? status : plan->d_status);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }

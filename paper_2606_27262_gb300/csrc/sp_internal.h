@@ -90,8 +90,9 @@ int compute_delays(const double *freqs, int32_t nchan, double tsamp, const doubl
 // plain input of n_in rows).
 int launch_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_staged,
                        int64_t pitch, cudaStream_t stream, int64_t row0 = 0, int64_t ring_rows = 0);
+// status: the device word a timed-out wait flags (nullptr: the plan's own).
 int launch_dedisperse(const sp_plan *plan, const uint8_t *d_xt, int64_t pitch, int64_t n_out,
-                      int32_t *d_out, cudaStream_t stream);
+                      int32_t *d_out, cudaStream_t stream, int32_t *status = nullptr);
 // One beam of a batched dedispersion launch, as the kernel reads it.
 struct BatchBeamDev {
     const uint8_t *xt;             // staged beam

@@ -4,10 +4,11 @@
 // a threshold, and a 3x3 peak filter in the DM-time plane).
 //
 // Kernels:
-//   sps_stats_kernel   one CTA per (row, normalisation block): exact int64
-//                      sum and sum of squares (16-byte loads), the 128-bit
-//                      variance term, and per-width float coefficients of
-//                      the S/N affine map.
+//   sps_stats_kernel   one CTA per (row, normalisation block): exact sum
+//                      (64-bit) and sum of squares (128-bit: int32 values
+//                      near 2^31 square to 2^62 each), 16-byte loads, the
+//                      128-bit variance term, and per-width float
+//                      coefficients of the S/N affine map.
 //   sps_boxcar_kernel  one CTA per 14 rows x 256 samples (+1 halo row and
 //                      sample on each side).  Stages prefix sums of the rows
 //                      in shared memory (warp-shuffle scans), evaluates every
@@ -46,39 +47,60 @@ __device__ __forceinline__ int64_t warp_sum_i64(int64_t v) {
     return v;
 }
 
+using u128 = unsigned __int128;
+
+__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)v, o);
+        const uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(v >> 64), o);
+        v += ((u128)hi << 64) | lo;
+    }
+    return v;
+}
+
+// x*x of an int32 is at most 2^62, so two squares add without overflow in
+// 64 bits before they join the 128-bit sum.
+__device__ __forceinline__ uint64_t sq2(int32_t a, int32_t b) {
+    return (uint64_t)((int64_t)a * a) + (uint64_t)((int64_t)b * b);
+}
+
 __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restrict__ dmt, int64_t n_out,
                                                         int64_t norm_block, int64_t nblk, WidthList wl,
                                                         int32_t *__restrict__ m0_out,
                                                         float2 *__restrict__ coef_out) {
-    __shared__ int64_t red1[8], red2[8];
+    __shared__ int64_t red1[8];
+    __shared__ u128 red2[8];
     const int64_t b = blockIdx.x;
     const int64_t d = blockIdx.y;
     const int64_t lo = (nblk == 1) ? 0 : b * norm_block;
     const int64_t hi = (b == nblk - 1) ? n_out : (b + 1) * norm_block;
     const int32_t *row = dmt + d * n_out;
-    int64_t s1 = 0, s2 = 0;
+    int64_t s1 = 0;
+    u128 s2 = 0;
     // Scalar head up to a 16-byte boundary, 16-byte body, scalar tail.
     const int64_t head = min(hi, lo + (int64_t)((4 - (((uintptr_t)(row + lo) >> 2) & 3)) & 3));
     const int64_t nvec = (hi - head) / 4;
     for (int64_t t = lo + threadIdx.x; t < head; t += 256) {
-        const int64_t x = __ldg(row + t);
+        const int32_t x = __ldg(row + t);
         s1 += x;
-        s2 += x * x;
+        s2 += sq2(x, 0);
     }
     const int4 *vrow = reinterpret_cast<const int4 *>(row + head);
 #pragma unroll 4
     for (int64_t i = threadIdx.x; i < nvec; i += 256) {  // four 16-byte loads in flight per thread
         const int4 q = __ldg(vrow + i);
         s1 += (int64_t)q.x + q.y + (int64_t)q.z + q.w;
-        s2 += (int64_t)q.x * q.x + (int64_t)q.y * q.y + (int64_t)q.z * q.z + (int64_t)q.w * q.w;
+        s2 += sq2(q.x, q.y);
+        s2 += sq2(q.z, q.w);
     }
     for (int64_t t = head + 4 * nvec + threadIdx.x; t < hi; t += 256) {
-        const int64_t x = __ldg(row + t);
+        const int32_t x = __ldg(row + t);
         s1 += x;
-        s2 += x * x;
+        s2 += sq2(x, 0);
     }
     s1 = warp_sum_i64(s1);
-    s2 = warp_sum_i64(s2);
+    s2 = warp_sum_u128(s2);
     if ((threadIdx.x & 31) == 0) {
         red1[threadIdx.x >> 5] = s1;
         red2[threadIdx.x >> 5] = s2;
@@ -87,7 +109,8 @@ __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restric
     __shared__ double s_frac, s_inv_sigma;
     const int64_t idx = d * nblk + b;
     if (threadIdx.x == 0) {
-        int64_t S1 = 0, S2 = 0;
+        int64_t S1 = 0;
+        u128 S2 = 0;
         for (int i = 0; i < 8; ++i) {
             S1 += red1[i];
             S2 += red2[i];
@@ -96,7 +119,8 @@ __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restric
         int64_t m0 = S1 / n;
         if (S1 - m0 * n < 0) --m0;  // floor for negative sums
         s_frac = (double)(S1 - m0 * n) / (double)n;
-        const __int128 var_n2 = (__int128)n * S2 - (__int128)S1 * S1;
+        // n <= 2^31 and S2 <= n * 2^62: the product stays below 2^124.
+        const __int128 var_n2 = (__int128)n * (__int128)S2 - (__int128)S1 * S1;
         s_inv_sigma = var_n2 > 0 ? (double)n / sqrt((double)var_n2) : 0.0;
         m0_out[idx] = (int32_t)m0;
     }

@@ -12,7 +12,11 @@
 // The array below exists once per device that loads the library and stays
 // resident until the process exits.  Host code cannot use its name as a
 // device address; the address is looked up per device with
-// cudaGetSymbolAddress the first time the entry point runs on that device.
+// cudaGetSymbolAddress the first time the entry point runs on that device
+// and kept for the life of the process.  It belongs to the device's primary
+// context: a cudaDeviceReset destroys that context, and the kept address is
+// stale afterwards, so this entry point must not be used on a device after
+// it was reset.
 #include <mutex>
 
 #include "sp_internal.h"

@@ -71,6 +71,11 @@ struct Launch {  // one batch in flight on one launch stream
     BatchBeamDev *d_table = nullptr;
     int64_t *d_begin = nullptr;
     unsigned long long *d_counter = nullptr;
+    // Status word of this batch's dedispersion (SP_STATUS_* bits), cleared
+    // before each launch and read back with the candidates: a bounded wait
+    // that ran out in any CTA invalidates every gulp of the batch.
+    int32_t *d_status = nullptr;
+    int32_t *h_status = nullptr;      // pinned
 };
 
 void CUDART_CB mark_done(void *p) {  // host callback: no CUDA calls here
@@ -226,6 +231,8 @@ void stream_free(sp_stream *s) {
         cudaFree(l.d_table);
         cudaFree(l.d_begin);
         cudaFree(l.d_counter);
+        cudaFree(l.d_status);
+        cudaFreeHost(l.h_status);
         if (s->streams[i]) cudaStreamDestroy(s->streams[i]);
     }
     for (Slot &sl : s->slots) {
@@ -312,11 +319,12 @@ int launch_batch(sp_stream *s, int li) {
     }
     const sp_plan *p = s->plan;
     int rc = SP_OK;
+    if (cudaMemsetAsync(L.d_status, 0, sizeof(int32_t), st) != cudaSuccess) rc = SP_ECUDA;
     for (int i = 0; i < n && !rc; ++i) rc = stage_gulp(s, L.gulps[i], s->slots[L.slots[i]], st);
     if (!rc && (s->flags & SP_STREAM_PER_GULP)) {
         for (int i = 0; i < n && !rc; ++i) {
             const Slot &sl = s->slots[L.slots[i]];
-            rc = launch_dedisperse(p, sl.d_staged, s->pitch, s->gulp, sl.d_dmt, st);
+            rc = launch_dedisperse(p, sl.d_staged, s->pitch, s->gulp, sl.d_dmt, st, L.d_status);
         }
     } else if (!rc) {
         const int64_t items = (int64_t)p->ntiles * dedisp_time_tiles(p, s->gulp);
@@ -351,7 +359,7 @@ int launch_batch(sp_stream *s, int li) {
         B.d_beams = L.d_table;
         B.d_item_begin = L.d_begin;
         B.d_counter = L.d_counter;
-        B.d_status = p->d_status;
+        B.d_status = L.d_status;
         // A persistent grid holds every SM until the batch is done, so the
         // classifier's kernels could not start before then; with a
         // classifier attached each item gets its own CTA, and the
@@ -362,6 +370,8 @@ int launch_batch(sp_stream *s, int li) {
     // dedispersion (already queued on the other launch stream) would
     // otherwise take the SMs first and hold this batch's results back until
     // it ends.
+    if (!rc && cudaMemcpyAsync(L.h_status, L.d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = SP_ECUDA;
     cudaStream_t ss = st;
     if (!rc && s->search_stream) {
         if (cudaEventRecord(L.dedispersed, st) != cudaSuccess ||
@@ -542,10 +552,15 @@ int progress(sp_stream *s) {
             g.r.info.t0 = L.gulps[i].seq * s->gulp;
             g.r.info.count = *sl.h_count;
             g.r.info.status = *sl.h_count > s->cap ? SP_EOVERFLOW : SP_OK;
+            if (*L.h_status & SP_STATUS_STAGING_TIMEOUT) {  // the whole batch is void
+                g.r.info.status = SP_ETIMEOUT;
+                g.r.info.count = 0;
+            }
             g.r.info.t_push = L.gulps[i].t_push;
             g.r.info.t_done = L.t_done;
             g.r.info.t_search = L.t_done;
-            g.r.cands.assign(sl.h_cands, sl.h_cands + std::min(*sl.h_count, s->cap));
+            if (g.r.info.status != SP_ETIMEOUT)
+                g.r.cands.assign(sl.h_cands, sl.h_cands + std::min(*sl.h_count, s->cap));
             g.slot = L.slots[i];
             if (!hold) s->free_slots.push_back(g.slot);
             s->searched.push_back(std::move(g));
@@ -642,6 +657,8 @@ extern "C" int sp_stream_create(const sp_plan *plan, int32_t nbeams, int64_t gul
         if (!rc) rc = alloc_dev((void **)&L.d_table, (int64_t)max_batch * sizeof(BatchBeamDev), &s->device_bytes);
         if (!rc) rc = alloc_dev((void **)&L.d_begin, (int64_t)(max_batch + 1) * 8, &s->device_bytes);
         if (!rc) rc = alloc_dev((void **)&L.d_counter, 8, &s->device_bytes);
+        if (!rc) rc = alloc_dev((void **)&L.d_status, 4, &s->device_bytes);
+        if (!rc) rc = alloc_host((void **)&L.h_status, 4);
         if (!rc && (cudaStreamCreateWithFlags(&s->streams[li], cudaStreamNonBlocking) != cudaSuccess ||
                     cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
                     cudaEventCreateWithFlags(&L.dedispersed, cudaEventDisableTiming) != cudaSuccess)) {

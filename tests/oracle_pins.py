@@ -194,6 +194,25 @@ def pin_snr_blocks(lib):
     assert sx[0, 1] == int(b.sum()) and sxx[0, 0] == int((a * a).sum())
 
 
+def pin_snr_large_values(lib):
+    """Values near +-2^30 over 4096-sample blocks: the sum of squares
+    (~2^72) exceeds 64 bits.  The moments must equal Python's exact integer
+    sums and the width-1 S/N must equal numpy's standardisation; a 64-bit sum
+    of squares wraps and fails both."""
+    rng = np.random.default_rng(11)
+    row = (rng.choice([-1, 1], 8192) * (2 ** 30 + rng.integers(0, 2 ** 20, 8192))).astype(np.int32)[None]
+    cnt, sx, sxx = oracle.moments(row, 4096, lib=lib)
+    for b in range(2):
+        seg = [int(v) for v in row[0, 4096 * b:4096 * (b + 1)]]
+        assert cnt[0, b] == 4096 and sx[0, b] == sum(seg)
+        assert sxx[0, b] == sum(v * v for v in seg) and sxx[0, b] > 2 ** 63
+    s = oracle.boxcar_snr(row, [1], 4096, lib=lib)[0, 0]
+    x = row[0].astype(np.float64)
+    for b in range(2):
+        seg = x[4096 * b:4096 * (b + 1)]
+        assert np.allclose(s[4096 * b:4096 * (b + 1)], (seg - seg.mean()) / seg.std(), rtol=1e-9, atol=1e-9)
+
+
 def pin_snr_zero_variance(lib):
     row = np.full((1, 64), 12345, np.int32)
     s = oracle.boxcar_snr(row, [1, 2, 4], 0, lib=lib)[0]
@@ -306,6 +325,6 @@ def pin_burst_recovered(lib):
 ALL_PINS = [
     pin_delays_exact, pin_delays_structure, pin_dedisperse_bruteforce, pin_dm0_channel_sum,
     pin_smearing_appendix_a, pin_snr_width1_standardisation, pin_snr_impulse_closed_form,
-    pin_snr_blocks, pin_snr_zero_variance, pin_snr_white_noise, pin_best_and_peaks_bruteforce,
+    pin_snr_blocks, pin_snr_large_values, pin_snr_zero_variance, pin_snr_white_noise, pin_best_and_peaks_bruteforce,
     pin_burst_recovered,
 ]

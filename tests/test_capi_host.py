@@ -37,8 +37,9 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_strerror(lib):
-    for code in (0, -1, -2, -3, -4, -5, -6, -7, -99):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8, -99):
         assert isinstance(lib.sp_strerror(code), bytes)
+    assert lib.sp_strerror(sp.SP_ETIMEOUT).startswith(b"a bounded wait")
     assert lib.sp_strerror(-2).startswith(b"inconsistent")
 
 
@@ -183,3 +184,21 @@ def test_staging_tables_sound_for_every_workload(lib, shape):
         assert rep["smem_bytes"] <= 227 * 1024, rep
     with pytest.raises(sp.SpotlightError):
         sp.plan_check_tables(c1.freqs, c1.tsamp, c1.dms, 7, 100)  # no such shape
+
+
+def test_noalloc_rejects_requests_beyond_its_scratch(lib):
+    """The allocation-free search refuses, before any CUDA call, a request
+    whose block statistics exceed its fixed 16 MiB array.  No device buffer
+    is involved: the DM transform pointer is never dereferenced, and the
+    candidate count is NULL so that even a regressed size check would stop
+    at the argument check instead of launching anything."""
+    huge_rows, n_out, L = 65535, 4096 * 64, 64  # statistics for 65535 rows x 4096 blocks
+    assert sp.sps_workspace_bytes(huge_rows, n_out, 2, L) > sp.SP_NOALLOC_SCRATCH_BYTES
+    w = np.array([1, 2], np.int32)
+    fake = ctypes.c_void_p(16)
+    rc = lib.sp_single_pulse_search_noalloc(fake, huge_rows, n_out, w.ctypes.data, 2, ctypes.c_float(6.0), L,
+                                            None, 0, None, None)
+    assert rc == sp.SP_ELIMIT
+    # within the limit the same NULL count is an argument error, still without a GPU
+    small = sp.sps_workspace_bytes(8, 1024, 2, 0)
+    assert 0 < small <= sp.SP_NOALLOC_SCRATCH_BYTES

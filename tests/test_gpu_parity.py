@@ -127,6 +127,7 @@ SPS_CASES = [
     (1, 1, [1], 0, "noise"),
     (29, 2600, list(range(1, 17)), 500, "noise"),           # 16 widths
     (10, 1000, [1, 4, 64, 256], 300, "huge"),               # |window sums| >= 2^31: 64-bit path
+    (6, 9000, [1, 2, 8, 32], 4096, "near_int32_max"),       # sums of squares beyond 2^63
 ]
 
 
@@ -137,6 +138,9 @@ def _dmt_values(kind, ndm, n_out, rng):
         return rng.integers(-50000, 50000, size=(ndm, n_out)).astype(np.int32)
     if kind == "huge":
         return rng.integers(-10_000_000, 10_000_000, size=(ndm, n_out)).astype(np.int32)
+    if kind == "near_int32_max":
+        sign = rng.choice([-1, 1], size=(ndm, n_out))
+        return (sign * (2 ** 30 + rng.integers(0, 2 ** 29, size=(ndm, n_out)))).astype(np.int32)
     return np.full((ndm, n_out), 777, np.int32)
 
 

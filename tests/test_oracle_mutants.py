@@ -27,6 +27,8 @@ MUTANTS = {
     "mean_term_dropped": ("(__int128)n * S - (__int128)w * s1", "(__int128)n * S - (__int128)s1"),
     "block_of_window_end": ("int64_t b = t / (norm_block > 0 ? norm_block : n_out);",
                             "int64_t b = (t + w - 1) / (norm_block > 0 ? norm_block : n_out);"),
+    "sum_of_squares_64bit": ("s2 += (__int128)((int64_t)row[t] * row[t]);",
+                             "s2 = (int64_t)((uint64_t)s2 + (uint64_t)((int64_t)row[t] * row[t]));"),
     "sample_variance": ("(__int128)n * s2 - (__int128)s1 * s1",
                         "((__int128)n * s2 - (__int128)s1 * s1) * n / (n > 1 ? n - 1 : 1)"),
     "widest_on_ties": ("if (kb < 0 || v > b) {", "if (kb < 0 || v >= b) {"),

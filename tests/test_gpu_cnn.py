@@ -69,6 +69,7 @@ def test_forward_gradients_and_adam_vs_oracle():
     assert np.allclose(prob.cpu().numpy(), po, atol=2e-3)
     assert abs(loss - lo) <= 2e-3 * abs(lo) + 1e-5
     # per tensor: relative L2 error and direction
+    worst = 0.0
     for (gl, ghw, ghb), (ol, ohw, ohb) in zip(ocnn.unpack(g), ocnn.unpack(go)):
         for (gw, gb), (ow, ob) in zip(gl + [(ghw, np.array([ghb]))], ol + [(ohw, np.array([ohb]))]):
             for a, b in ((gw, ow), (gb, ob)):
@@ -76,7 +77,9 @@ def test_forward_gradients_and_adam_vs_oracle():
                 nrm = np.linalg.norm(b)
                 assert np.linalg.norm(a - b) <= 3e-2 * nrm + 1e-7, (np.linalg.norm(a - b), nrm)
                 if nrm > 1e-6:
+                    worst = max(worst, np.linalg.norm(a - b) / nrm)
                     assert a @ b / (np.linalg.norm(a) * nrm) >= 0.999
+    print(f"gradient parity: worst relative L2 error per tensor {worst:.3e}")
     # one Adam step from zero moments
     clf.adam_step(1e-3)
     p1 = clf.params()

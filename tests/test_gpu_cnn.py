@@ -68,14 +68,19 @@ def test_forward_gradients_and_adam_vs_oracle():
     po, lo, go = ocnn.forward_backward(p0.astype(np.float64), _as64(ft), _as64(dmt), labels, round_bf16=True)
     assert np.allclose(prob.cpu().numpy(), po, atol=2e-3)
     assert abs(loss - lo) <= 2e-3 * abs(lo) + 1e-5
-    # per tensor: relative L2 error and direction
+    # Per tensor: relative L2 error and direction.  The oracle rounds to
+    # bfloat16 at the GPU's storage points, so what remains is float32
+    # accumulation order (~1e-6) and the bf16 values that order flips to the
+    # neighbouring bf16 number (2^-8 relative each), carried through five
+    # layers of the backward pass: measured worst 1.0e-2 over all tensors;
+    # the bar is twice that.
     worst = 0.0
     for (gl, ghw, ghb), (ol, ohw, ohb) in zip(ocnn.unpack(g), ocnn.unpack(go)):
         for (gw, gb), (ow, ob) in zip(gl + [(ghw, np.array([ghb]))], ol + [(ohw, np.array([ohb]))]):
             for a, b in ((gw, ow), (gb, ob)):
                 a, b = np.ravel(a), np.ravel(b)
                 nrm = np.linalg.norm(b)
-                assert np.linalg.norm(a - b) <= 3e-2 * nrm + 1e-7, (np.linalg.norm(a - b), nrm)
+                assert np.linalg.norm(a - b) <= 2e-2 * nrm + 1e-7, (np.linalg.norm(a - b), nrm)
                 if nrm > 1e-6:
                     worst = max(worst, np.linalg.norm(a - b) / nrm)
                     assert a @ b / (np.linalg.norm(a) * nrm) >= 0.999

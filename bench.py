@@ -86,6 +86,8 @@ def parse_args(argv=None):
                    help="searched samples per beam (default: the full 131072); smaller values are for "
                         "profiler captures only")
     p.add_argument("--workload", choices=["single", "batched", "stream", "classifier"], default="single")
+    p.add_argument("--shape", type=int, default=None,
+                   help="single workload: dedispersion kernel shape (default: the library's default plan)")
     p.add_argument("--stream-beams", type=int, default=256, help="stream workload: beams")
     p.add_argument("--stream-periods", type=float, default=3.0,
                    help="stream workload: gulp periods of real-time arrivals for the latency figures")
@@ -254,7 +256,8 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     spbuild.build()
     wl = workload(args.n_out)
-    plan = sp.Plan(wl.freqs, wl.tsamp, wl.dms)
+    plan = sp.Plan(wl.freqs, wl.tsamp, wl.dms) if args.shape is None else \
+        sp.Plan(wl.freqs, wl.tsamp, wl.dms, shape=args.shape)
     n_in = wl.n_out + plan.max_delay
     x, _ = synth.make_workload_beam(wl, n_in, seed=beam_seed(wl.seed, rank))
 
@@ -320,16 +323,32 @@ def run_ours(args):
         h_in = torch.from_numpy(x).pin_memory()
         hc = np.empty((cap, 4), np.int32)
         s.run_host(h_in, hc)
+        s.submit_host(h_in)  # first submit allocates the second slot
+        s.collect(hc)
+        # one beam at a time: copy in, search, results out, then the next
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.run_host(h_in, hc)
+        serial_s = reduce_max(time.perf_counter() - t0, world, dev) / args.steps
+        # beams back to back: each beam's input copy overlaps the search of
+        # the beam before it; every step still copies its whole input in and
+        # its candidates out
         barrier(world)
         t0 = time.perf_counter()
         n_found = 0
-        for _ in range(args.steps):
-            n_found = s.run_host(h_in, hc)
+        s.submit_host(h_in)
+        for k in range(args.steps):
+            if k + 1 < args.steps:
+                s.submit_host(h_in)
+            n_found = s.collect(hc)
         e2e_s = reduce_max(time.perf_counter() - t0, world, dev) / args.steps
         barrier(world)
         e2e = {"value": world * beam_s / e2e_s, "unit": "beams", "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": 8 + 16 * min(n_found, cap),
-               "api": "sp_searcher_run_host"}
+               "api": "sp_searcher_submit_host + sp_searcher_collect (two beams in flight)",
+               "serial": {"value": world * beam_s / serial_s, "ms_per_step": serial_s * 1e3,
+                          "api": "sp_searcher_run_host (one beam at a time)"}}
         s.close()
 
     cpu = None
@@ -348,6 +367,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(wl.n_out),
                      "kernel": "dedisperse_kernel",
+                     "kernel_shape": dict(zip(("dm_tile", "time_tile", "chan_chunk"), sp.shape_info(plan.shape)))
+                     | {"shape": plan.shape, "dm_tiles": plan.ntiles},
                      "peak_basis": f"{nsm} SMs x {lanes:.1f} measured 32-bit add lanes/SM/clk x "
                                    f"{MAX_SM_MHZ:.0f} MHz"},
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,

@@ -138,7 +138,7 @@ int sp_compute_delays(const double *freqs_mhz, int32_t nchan, double tsamp_s,
  *   cached timings without launching anything.
  * Errors: SP_EINVAL (bad shape or arguments, n_out_sample < 1, reps < 1),
  *   the plan-creation errors, SP_ENOMEM, SP_ECUDA. */
-#define SP_DEDISP_NUM_SHAPES 3
+#define SP_DEDISP_NUM_SHAPES 4
 #define SP_SHAPE_AUTO (-1)
 #define SP_AUTOTUNE_SAMPLES 16384
 #define SP_AUTOTUNE_REPS 3
@@ -322,6 +322,25 @@ int sp_searcher_run(sp_searcher *s, const uint8_t *d_in, sp_cand *d_cands, int64
  * (after filling h_cands) when the total exceeds min(cap, cand_cap). */
 int sp_searcher_run_host(sp_searcher *s, const uint8_t *h_in, sp_cand *h_cands, int64_t cap,
                          int64_t *h_count, void *stream);
+/* Pipelined end-to-end runs from host memory, for a sequence of beams: the
+ * copy of one beam's input overlaps the search of the beam before it
+ * (Sec. 2: beams arrive continuously and each GPU searches them back to
+ * back).  sp_searcher_submit_host queues one beam and returns at once: its
+ * h_in [n_in][nchan] is copied on a copy stream of the searcher into one of
+ * two device input buffers (after the beam that last used that buffer has
+ * been staged), then dedispersed and searched on `stream`, and its count
+ * copied to page-locked memory of the searcher.  h_in must be page-locked
+ * for the copy to overlap, and must stay unchanged until that beam has been
+ * collected.  At most two beams are uncollected at a time (SP_EINVAL for a
+ * third).  sp_searcher_collect waits for the oldest uncollected beam and
+ * copies its first min(count, cap, cand_cap) candidates to h_cands and its
+ * total to *h_count; SP_EOVERFLOW (after copying) when the total exceeds
+ * that, SP_EINVAL when nothing is queued.  The first submit allocates the
+ * second input buffer, the second candidate buffer, two streams and four
+ * events; later calls allocate nothing.  Results come back in submission
+ * order, each equal to sp_searcher_run_host of the same input. */
+int sp_searcher_submit_host(sp_searcher *s, const uint8_t *h_in, void *stream);
+int sp_searcher_collect(sp_searcher *s, sp_cand *h_cands, int64_t cap, int64_t *h_count);
 
 /* ----------------------------------------------------------------- batch --
  * A fixed set of beams searched as one step: the multi-beam workload of one

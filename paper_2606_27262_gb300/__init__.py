@@ -73,6 +73,8 @@ SIGNATURES = {
     "sp_searcher_destroy": (ctypes.c_int, [P]),
     "sp_searcher_run": (ctypes.c_int, [P, P, P, I64, P, P]),
     "sp_searcher_run_host": (ctypes.c_int, [P, P, P, I64, P, P]),
+    "sp_searcher_submit_host": (ctypes.c_int, [P, P, P]),
+    "sp_searcher_collect": (ctypes.c_int, [P, P, I64, P]),
     "sp_dedisp_shape_info": (ctypes.c_int, [I32, P, P, P]),
     "sp_plan_create_shaped": (ctypes.c_int, [P, I32, F64, P, I32, I32, P]),
     "sp_plan_shape": (ctypes.c_int, [P, P, P, P]),
@@ -121,7 +123,7 @@ SIGNATURES = {
     "sp_cnn_extract": (ctypes.c_int, [P, P, I64, I64, P, I32, P, I32, I32, P, P]),
     "sp_probe_iadd3_rate": (ctypes.c_int, [ctypes.c_int, P, P]),
 }
-SP_DEDISP_NUM_SHAPES = 3
+SP_DEDISP_NUM_SHAPES = 4
 SP_SHAPE_AUTO = -1
 SP_AUTOTUNE_SAMPLES = 16384
 SP_AUTOTUNE_REPS = 3
@@ -361,6 +363,20 @@ class Searcher:
                                          ctypes.byref(cnt), _stream(stream))
         if rc not in (SP_OK, SP_EOVERFLOW):
             _check(rc, "sp_searcher_run_host")
+        return int(cnt.value)
+
+    def submit_host(self, h_in, stream=None):
+        """Queues one beam from host memory (page-locked for overlap); at
+        most two uncollected beams.  h_in must stay unchanged until collected."""
+        _check(_lib().sp_searcher_submit_host(self._h, _ptr(h_in), _stream(stream)), "sp_searcher_submit_host")
+
+    def collect(self, h_cands: np.ndarray) -> int:
+        """Waits for the oldest submitted beam; fills h_cands (int32 [cap][4])
+        and returns its total count."""
+        cnt = ctypes.c_int64()
+        rc = _lib().sp_searcher_collect(self._h, h_cands.ctypes.data, h_cands.shape[0], ctypes.byref(cnt))
+        if rc not in (SP_OK, SP_EOVERFLOW):
+            _check(rc, "sp_searcher_collect")
         return int(cnt.value)
 
     def close(self):

@@ -199,6 +199,21 @@ struct sp_searcher {
     int64_t sps_bytes = 0;
     sp_cand *d_cands = nullptr;
     int64_t *d_count = nullptr;
+    // Pipelined host runs (sp_searcher_submit_host): two slots, each with
+    // its device input, candidates and count, a page-locked count, and the
+    // events that order the input copy after the slot's last staging and
+    // the collection after the slot's search.  Slot 0 uses d_in, d_cands
+    // and d_count above.
+    bool pipe_ready = false;
+    uint8_t *p_in[2] = {nullptr, nullptr};
+    sp_cand *p_cands[2] = {nullptr, nullptr};
+    int64_t *p_count[2] = {nullptr, nullptr};
+    int64_t *h_count = nullptr;      // page-locked [2]
+    cudaStream_t copy_stream = nullptr, result_stream = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, staged[2] = {nullptr, nullptr};
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    bool staged_used[2] = {false, false};
+    int head = 0, queued = 0;        // oldest uncollected slot, uncollected beams
 };
 
 static void searcher_free(sp_searcher *s) {
@@ -208,6 +223,17 @@ static void searcher_free(sp_searcher *s) {
     cudaFree(s->d_sps);
     cudaFree(s->d_cands);
     cudaFree(s->d_count);
+    cudaFree(s->p_in[1]);
+    cudaFree(s->p_cands[1]);
+    cudaFree(s->p_count[1]);
+    cudaFreeHost(s->h_count);
+    for (int i = 0; i < 2; ++i) {
+        if (s->copied[i]) cudaEventDestroy(s->copied[i]);
+        if (s->staged[i]) cudaEventDestroy(s->staged[i]);
+        if (s->done[i]) cudaEventDestroy(s->done[i]);
+    }
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    if (s->result_stream) cudaStreamDestroy(s->result_stream);
 }
 
 extern "C" int sp_searcher_create(const sp_plan *p, int64_t n_out, const int32_t *h_widths, int32_t nw,
@@ -285,5 +311,86 @@ extern "C" int sp_searcher_run_host(sp_searcher *s, const uint8_t *h_in, sp_cand
             cudaStreamSynchronize(st) != cudaSuccess)
             return SP_ECUDA;
     }
+    return total > cap_eff ? SP_EOVERFLOW : SP_OK;
+}
+
+// Second slot, streams and events of the pipelined host path (first submit).
+static int searcher_pipe_init(sp_searcher *s) {
+    if (s->pipe_ready) return SP_OK;
+    const size_t in_bytes = (size_t)(s->n_in * s->plan->nchan);
+    s->p_in[0] = s->d_in;
+    s->p_cands[0] = s->d_cands;
+    s->p_count[0] = s->d_count;
+    bool ok = cudaMalloc((void **)&s->p_in[1], in_bytes) == cudaSuccess &&
+              cudaMalloc((void **)&s->p_cands[1], (size_t)std::max<int64_t>(1, s->cap) * sizeof(sp_cand)) ==
+                  cudaSuccess &&
+              cudaMalloc((void **)&s->p_count[1], sizeof(int64_t)) == cudaSuccess &&
+              cudaMallocHost((void **)&s->h_count, 2 * sizeof(int64_t)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return SP_ENOMEM;
+    }
+    ok = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&s->result_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < 2; ++i)
+        ok = cudaEventCreateWithFlags(&s->copied[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->staged[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->done[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return SP_ECUDA;
+    }
+    s->pipe_ready = true;
+    return SP_OK;
+}
+
+extern "C" int sp_searcher_submit_host(sp_searcher *s, const uint8_t *h_in, void *stream) {
+    if (!s || !h_in || s->queued >= 2) return SP_EINVAL;
+    int rc = check_dedisp_shape(s->plan, s->n_in, s->n_out);
+    if (!rc) rc = searcher_pipe_init(s);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int i = (s->head + s->queued) % 2;
+    // The slot's input is rewritten only after its previous beam was staged.
+    if (s->staged_used[i] && cudaStreamWaitEvent(s->copy_stream, s->staged[i], 0) != cudaSuccess) return SP_ECUDA;
+    if (cudaMemcpyAsync(s->p_in[i], h_in, (size_t)(s->n_in * s->plan->nchan), cudaMemcpyHostToDevice,
+                        s->copy_stream) != cudaSuccess ||
+        cudaEventRecord(s->copied[i], s->copy_stream) != cudaSuccess ||
+        cudaStreamWaitEvent(st, s->copied[i], 0) != cudaSuccess)
+        return SP_ECUDA;
+    const int64_t pitch = dedisp_pitch(s->n_in);
+    uint8_t *staged = static_cast<uint8_t *>(s->d_work);
+    rc = launch_stage_input(s->p_in[i], s->n_in, s->plan->nchan, staged, pitch, st);
+    if (!rc && cudaEventRecord(s->staged[i], st) != cudaSuccess) rc = SP_ECUDA;
+    if (rc) return rc;
+    s->staged_used[i] = true;
+    rc = sp_dedisperse_staged(s->plan, staged, pitch, s->n_in, s->d_dmt, s->n_out, stream);
+    if (!rc)
+        rc = sp_single_pulse_search(s->d_dmt, s->plan->ndm, s->n_out, s->widths, s->nw, s->threshold,
+                                    s->norm_block, s->d_sps, s->sps_bytes, s->p_cands[i], s->cap, s->p_count[i],
+                                    stream);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(s->h_count + i, s->p_count[i], sizeof(int64_t), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaEventRecord(s->done[i], st) != cudaSuccess)
+        return SP_ECUDA;
+    ++s->queued;
+    return SP_OK;
+}
+
+extern "C" int sp_searcher_collect(sp_searcher *s, sp_cand *h_cands, int64_t cap, int64_t *h_count) {
+    if (!s || !h_count || cap < 0 || (cap > 0 && !h_cands) || s->queued == 0) return SP_EINVAL;
+    const int i = s->head;
+    s->head = (s->head + 1) % 2;
+    --s->queued;
+    if (cudaEventSynchronize(s->done[i]) != cudaSuccess) return SP_ECUDA;
+    const int64_t total = s->h_count[i];
+    const int64_t cap_eff = std::min(cap, s->cap);
+    *h_count = total;
+    const int64_t n = std::min(total, cap_eff);
+    if (n > 0 && (cudaMemcpyAsync(h_cands, s->p_cands[i], (size_t)n * sizeof(sp_cand), cudaMemcpyDeviceToHost,
+                                  s->result_stream) != cudaSuccess ||
+                  cudaStreamSynchronize(s->result_stream) != cudaSuccess))
+        return SP_ECUDA;
     return total > cap_eff ? SP_EOVERFLOW : SP_OK;
 }

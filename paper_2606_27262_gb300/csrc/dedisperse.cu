@@ -149,8 +149,20 @@ __device__ __forceinline__ void add_quad(uint32_t wa, uint32_t wb, uint32_t wc, 
     acc[3] = (int32_t)__dp4a(__byte_perm(t1, t3, 0x7632), 0x01010101u, (uint32_t)acc[3]);
 }
 
+// Packed 8-DM sums: for one channel's word w (samples t..t+3 in bytes 0..3)
+// the raw word is added to S and its odd bytes, moved into the low byte of
+// each 16-bit lane, to H.  After n <= 257 channels every 16-bit lane of H
+// holds an exact sum (samples t+1 and t+3), and S - (H << 8) holds samples
+// t and t+2 in its 16-bit lanes: the carries out of the even bytes of S are
+// exactly the odd-byte sums that H removes.  Two channels per call, so that
+// each sum is one 3-input add.
+__device__ __forceinline__ void add_packed(uint32_t wa, uint32_t wb, uint32_t &S, uint32_t &H) {
+    S = S + wa + wb;
+    H = H + __byte_perm(wa, 0u, 0x4341) + __byte_perm(wb, 0u, 0x4341);
+}
+
 // Shared-memory layout (bytes), for a shape with CH channels per chunk and
-// DT = 4*CH trial DMs per tile:
+// DT trial DMs per tile:
 //   [0, 8*NS)                 one mbarrier per raw slot
 //   [32, 40)                  work item of a persistent CTA
 //   [64, 64 + NS*CH*16)       geometry of the chunk in each raw slot
@@ -168,16 +180,25 @@ __device__ __forceinline__ void add_quad(uint32_t wa, uint32_t wb, uint32_t wc, 
 // it into copies buffer (k+1) & 1; barrier.  A raw slot is refilled two
 // barriers after its chunk was expanded; a copies buffer one barrier after
 // its chunk was summed.
-template <int CH, int SPT>
+//
+// A shape has NDT = 4 or 8 trial DMs per thread (DT = NDT*CH per tile).
+// With 4, a thread keeps 4 DMs x SPT int32 sums.  With 8, a tile of more than
+// 4*CH DMs keeps per DM and 4-sample word two packed 16-bit-lane partials
+// (add_packed) -- the same registers as 4 DMs of int32 sums -- and adds
+// them to the output every kDedispPackedChannels channels; a smaller tile of
+// that shape runs with 4 DMs per thread.  Eight DMs per thread halve the
+// copy expansion, the offset-table traffic and the barriers per add.
+template <int CH, int SPT, int NDT>
 struct Shape {
-    static constexpr int NDT = kDedispDmPerThread;
     static constexpr int DT = NDT * CH;
     static constexpr int T = 32 * SPT;
     static constexpr int NQ = SPT / 4;  // 4-sample words per thread per row
     static constexpr int NS = kDedispRawSlots;
     static constexpr int HDR = dedisp_header_bytes(CH, DT);
     static constexpr int GROUP = kDedispTileGroupDms / DT;  // DM tiles per raster group
-    static_assert(NDT == 4, "offset table is read as int4 per thread");
+    static constexpr int FLUSH = kDedispPackedChannels / CH;  // chunks per packed flush
+    static_assert(NDT == 4 || NDT == 8, "offsets are read as int4 per 4 DMs");
+    static_assert(kDedispPackedChannels % CH == 0 && kDedispPackedChannels <= 257, "16-bit lanes");
     static_assert(SPT % 4 == 0 && T <= kDedispMaxTimeTile, "time tile");
     static_assert(CH <= kDedispMaxChanChunk && CH % 4 == 0, "the issuing warp's lanes copy one channel each; quads");
     static_assert(8 * NS <= kDedispItemOffset && kDedispItemOffset + 8 <= kDedispGeoOffset,
@@ -199,21 +220,22 @@ __device__ __forceinline__ void raster(int64_t id, int ntiles, int64_t ntime, in
     tq = r / width;
 }
 
-// One (DM tile, time tile) of one beam.  Returns false (uniformly across the
-// CTA) if a staging wait ran out; copies still in flight are waited for
-// (with the same bound) before it returns.
-template <int CH, int SPT>
-__device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const uint8_t *__restrict__ xt,
-                                            int64_t pitch, int32_t nchan, int32_t nchunks, int d_first, int d_cnt,
-                                            int64_t t0, const int4 *__restrict__ geo_g,
-                                            const int32_t *__restrict__ off_g, int32_t copies_max,
-                                            int32_t raw_max, int64_t n_out, int32_t *__restrict__ out) {
-    using S = Shape<CH, SPT>;
-    constexpr int NDT = S::NDT, DT = S::DT, NS = S::NS, NQ = S::NQ;
+// One (DM tile, time tile) of one beam, with DT = the shape's table stride
+// and PACKED = 8 DMs per thread.  Returns false (uniformly across the CTA)
+// if a staging wait ran out; copies still in flight are waited for (with
+// the same bound) before it returns.
+template <int CH, int SPT, int DT, bool PACKED>
+__device__ __forceinline__ bool dedisp_tile_body(uint8_t *smem, uint32_t seq0, const uint8_t *__restrict__ xt,
+                                                 int64_t pitch, int32_t nchan, int32_t nchunks, int d_first,
+                                                 int d_cnt, int64_t t0, const int4 *__restrict__ geo_g,
+                                                 const int32_t *__restrict__ off_g, int32_t copies_max,
+                                                 int32_t raw_max, int64_t n_out, int32_t *__restrict__ out) {
+    using S = Shape<CH, SPT, DT / CH>;
+    constexpr int NDT = PACKED ? 8 : 4, NS = S::NS, NQ = S::NQ, HDR = S::HDR, FLUSH = S::FLUSH;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);                       // [NS]
     int4 *geo_s = reinterpret_cast<int4 *>(smem + kDedispGeoOffset);           // [NS][CH]
     int32_t *offt_s = reinterpret_cast<int32_t *>(smem + kDedispOffTabOffset);  // [NS][CH*DT]
-    uint8_t *raw_s = smem + S::HDR;                                             // [NS][raw_max]
+    uint8_t *raw_s = smem + HDR;                                                // [NS][raw_max]
     uint8_t *cop_s = raw_s + NS * raw_max;                                      // [2][copies_max]
 
     const int warp = threadIdx.x >> 5;
@@ -301,11 +323,54 @@ __device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const 
         failed = __syncthreads_or(!ok);
     }
 
-    int32_t acc[NDT][SPT];
+    // 4 DMs: int32 sums acc[i][4q + j] of sample t0 + 128q + 4*lane + j.
+    // 8 DMs: packed partials pk[i][q] = {S, H} of the same samples.
+    constexpr int NACC = PACKED ? 1 : NDT;
+    constexpr int NPK = PACKED ? NDT : 1;
+    int32_t acc[NACC][SPT];
+    uint32_t pk[NPK][NQ][2];
 #pragma unroll
-    for (int i = 0; i < NDT; ++i)
+    for (int i = 0; i < NACC; ++i)
 #pragma unroll
         for (int j = 0; j < SPT; ++j) acc[i][j] = 0;
+#pragma unroll
+    for (int i = 0; i < NPK; ++i)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) pk[i][q][0] = pk[i][q][1] = 0u;
+    const bool vec = (n_out & 3) == 0;
+
+    // Adds the packed partials to the output (stores them on the first
+    // flush) and clears them.
+    auto flush = [&](bool first) {
+#pragma unroll
+        for (int i = 0; i < NPK; ++i) {
+            const int dl = warp * NDT + i;
+            if (dl >= d_cnt) continue;
+            int32_t *orow = out + (int64_t)(d_first + dl) * n_out;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const uint32_t H = pk[i][q][1], L = pk[i][q][0] - (H << 8);
+                const int32_t v0 = (int32_t)(L & 0xFFFFu), v1 = (int32_t)(H & 0xFFFFu);
+                const int32_t v2 = (int32_t)(L >> 16), v3 = (int32_t)(H >> 16);
+                pk[i][q][0] = pk[i][q][1] = 0u;
+                const int64_t t = t0 + 128 * q + 4 * lane;
+                if (vec && t + 3 < n_out) {
+                    int4 *dst = reinterpret_cast<int4 *>(orow + t);
+                    int4 cur = first ? zero4 : *dst;
+                    cur.x += v0;
+                    cur.y += v1;
+                    cur.z += v2;
+                    cur.w += v3;
+                    *dst = cur;
+                } else {
+                    const int32_t v[4] = {v0, v1, v2, v3};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (t + j < n_out) orow[t + j] = (first ? 0 : orow[t + j]) + v[j];
+                }
+            }
+        }
+    };
 
     for (int k = 0; k < nchunks; ++k) {
         const int b = k & 1;
@@ -320,40 +385,80 @@ __device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const 
         if (warp_active && !failed) {
             const uint8_t *sb = cop_s + b * copies_max + lane * 4;
             const int32_t *ot = offt_s + slot_of(k) * CH * DT + warp * NDT;
-            if (nc == CH) {
+            if constexpr (PACKED) {
+                if (nc == CH) {
 #pragma unroll
-                for (int qd = 0; qd < CH / 4; ++qd) {
-                    const int4 o0 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 0) * DT);
-                    const int4 o1 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 1) * DT);
-                    const int4 o2 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 2) * DT);
-                    const int4 o3 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 3) * DT);
-                    const int32_t a0[4] = {o0.x, o0.y, o0.z, o0.w}, a1[4] = {o1.x, o1.y, o1.z, o1.w};
-                    const int32_t a2[4] = {o2.x, o2.y, o2.z, o2.w}, a3[4] = {o3.x, o3.y, o3.z, o3.w};
+                    for (int cp = 0; cp < CH / 2; ++cp) {
+                        const int4 x0 = *reinterpret_cast<const int4 *>(ot + (2 * cp) * DT);
+                        const int4 x1 = *reinterpret_cast<const int4 *>(ot + (2 * cp) * DT + 4);
+                        const int4 y0 = *reinterpret_cast<const int4 *>(ot + (2 * cp + 1) * DT);
+                        const int4 y1 = *reinterpret_cast<const int4 *>(ot + (2 * cp + 1) * DT + 4);
+                        const int32_t oa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                        const int32_t ob[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
-                    for (int i = 0; i < NDT; ++i) {
+                        for (int i = 0; i < NDT; ++i) {
 #pragma unroll
-                        for (int q = 0; q < NQ; ++q) {
-                            const uint32_t wa = *reinterpret_cast<const uint32_t *>(sb + a0[i] + 128 * q);
-                            const uint32_t wb = *reinterpret_cast<const uint32_t *>(sb + a1[i] + 128 * q);
-                            const uint32_t wc = *reinterpret_cast<const uint32_t *>(sb + a2[i] + 128 * q);
-                            const uint32_t wd = *reinterpret_cast<const uint32_t *>(sb + a3[i] + 128 * q);
-                            add_quad(wa, wb, wc, wd, &acc[i][4 * q]);
+                            for (int q = 0; q < NQ; ++q) {
+                                const uint32_t wa = *reinterpret_cast<const uint32_t *>(sb + oa[i] + 128 * q);
+                                const uint32_t wb = *reinterpret_cast<const uint32_t *>(sb + ob[i] + 128 * q);
+                                add_packed(wa, wb, pk[i][q][0], pk[i][q][1]);
+                            }
+                        }
+                    }
+                } else {
+                    for (int c = 0; c < nc; ++c) {
+                        const int4 x0 = *reinterpret_cast<const int4 *>(ot + c * DT);
+                        const int4 x1 = *reinterpret_cast<const int4 *>(ot + c * DT + 4);
+                        const int32_t oa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                        for (int i = 0; i < NDT; ++i) {
+#pragma unroll
+                            for (int q = 0; q < NQ; ++q) {
+                                const uint32_t w = *reinterpret_cast<const uint32_t *>(sb + oa[i] + 128 * q);
+                                add_packed(w, 0u, pk[i][q][0], pk[i][q][1]);
+                            }
                         }
                     }
                 }
             } else {
-                for (int c = 0; c < nc; ++c) {
-                    const int4 oc = *reinterpret_cast<const int4 *>(ot + c * DT);
-                    const int32_t ac[4] = {oc.x, oc.y, oc.z, oc.w};
+                if (nc == CH) {
 #pragma unroll
-                    for (int i = 0; i < NDT; ++i) {
+                    for (int qd = 0; qd < CH / 4; ++qd) {
+                        const int4 o0 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 0) * DT);
+                        const int4 o1 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 1) * DT);
+                        const int4 o2 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 2) * DT);
+                        const int4 o3 = *reinterpret_cast<const int4 *>(ot + (4 * qd + 3) * DT);
+                        const int32_t a0[4] = {o0.x, o0.y, o0.z, o0.w}, a1[4] = {o1.x, o1.y, o1.z, o1.w};
+                        const int32_t a2[4] = {o2.x, o2.y, o2.z, o2.w}, a3[4] = {o3.x, o3.y, o3.z, o3.w};
 #pragma unroll
-                        for (int q = 0; q < NQ; ++q) {
-                            const uint32_t w = *reinterpret_cast<const uint32_t *>(sb + ac[i] + 128 * q);
-                            add_quad(w, 0u, 0u, 0u, &acc[i][4 * q]);
+                        for (int i = 0; i < NDT; ++i) {
+#pragma unroll
+                            for (int q = 0; q < NQ; ++q) {
+                                const uint32_t wa = *reinterpret_cast<const uint32_t *>(sb + a0[i] + 128 * q);
+                                const uint32_t wb = *reinterpret_cast<const uint32_t *>(sb + a1[i] + 128 * q);
+                                const uint32_t wc = *reinterpret_cast<const uint32_t *>(sb + a2[i] + 128 * q);
+                                const uint32_t wd = *reinterpret_cast<const uint32_t *>(sb + a3[i] + 128 * q);
+                                add_quad(wa, wb, wc, wd, &acc[i][4 * q]);
+                            }
+                        }
+                    }
+                } else {
+                    for (int c = 0; c < nc; ++c) {
+                        const int4 oc = *reinterpret_cast<const int4 *>(ot + c * DT);
+                        const int32_t ac[4] = {oc.x, oc.y, oc.z, oc.w};
+#pragma unroll
+                        for (int i = 0; i < NDT; ++i) {
+#pragma unroll
+                            for (int q = 0; q < NQ; ++q) {
+                                const uint32_t w = *reinterpret_cast<const uint32_t *>(sb + ac[i] + 128 * q);
+                                add_quad(w, 0u, 0u, 0u, &acc[i][4 * q]);
+                            }
                         }
                     }
                 }
+            }
+            if constexpr (PACKED) {
+                if ((k + 1) % FLUSH == 0 || k + 1 == nchunks) flush(k < FLUSH);
             }
         }
         bool ok = true;
@@ -370,29 +475,47 @@ __device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const 
     }
     if (failed) return false;
 
-    const bool vec = (n_out & 3) == 0;
+    if constexpr (!PACKED) {
 #pragma unroll
-    for (int i = 0; i < NDT; ++i) {
-        const int dl = warp * NDT + i;
-        if (dl >= d_cnt) continue;
-        int32_t *orow = out + (int64_t)(d_first + dl) * n_out;
+        for (int i = 0; i < NDT; ++i) {
+            const int dl = warp * NDT + i;
+            if (dl >= d_cnt) continue;
+            int32_t *orow = out + (int64_t)(d_first + dl) * n_out;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int64_t t = t0 + 128 * q + 4 * lane;
-            if (vec && t + 3 < n_out) {
-                *reinterpret_cast<int4 *>(orow + t) =
-                    make_int4(acc[i][4 * q], acc[i][4 * q + 1], acc[i][4 * q + 2], acc[i][4 * q + 3]);
-            } else {
+            for (int q = 0; q < NQ; ++q) {
+                const int64_t t = t0 + 128 * q + 4 * lane;
+                if (vec && t + 3 < n_out) {
+                    *reinterpret_cast<int4 *>(orow + t) =
+                        make_int4(acc[i][4 * q], acc[i][4 * q + 1], acc[i][4 * q + 2], acc[i][4 * q + 3]);
+                } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (t + j < n_out) orow[t + j] = acc[i][4 * q + j];
+                    for (int j = 0; j < 4; ++j)
+                        if (t + j < n_out) orow[t + j] = acc[i][4 * q + j];
+                }
             }
         }
     }
     return true;
 }
 
-template <int CH, int SPT>
+// One tile of a shape with NDT DMs per thread: tiles of more than 4*CH DMs
+// take the packed 8-DM body, the others the 4-DM body (same tables).
+template <int CH, int SPT, int NDT>
+__device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const uint8_t *__restrict__ xt,
+                                            int64_t pitch, int32_t nchan, int32_t nchunks, int d_first, int d_cnt,
+                                            int64_t t0, const int4 *__restrict__ geo_g,
+                                            const int32_t *__restrict__ off_g, int32_t copies_max,
+                                            int32_t raw_max, int64_t n_out, int32_t *__restrict__ out) {
+    constexpr int DT = NDT * CH;
+    if constexpr (NDT == 8) {
+        if (d_cnt > 4 * CH)
+            return dedisp_tile_body<CH, SPT, DT, true>(smem, seq0, xt, pitch, nchan, nchunks, d_first, d_cnt, t0,
+                                                       geo_g, off_g, copies_max, raw_max, n_out, out);
+    }
+    return dedisp_tile_body<CH, SPT, DT, false>(smem, seq0, xt, pitch, nchan, nchunks, d_first, d_cnt, t0, geo_g,
+                                                off_g, copies_max, raw_max, n_out, out);
+}
+
 __device__ __forceinline__ void init_barriers(uint8_t *smem) {
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
     if (threadIdx.x < kDedispRawSlots) mbar_init(&mbar[threadIdx.x], 1);
@@ -402,19 +525,19 @@ __device__ __forceinline__ void init_barriers(uint8_t *smem) {
 
 // One beam: grid = (DM tiles, time tiles), one (DM tile, time tile) per CTA
 // in raster order.
-template <int CH, int SPT>
+template <int CH, int SPT, int NDT>
 __global__ void __launch_bounds__(CH * 32, (CH == 8 ? 2 : 3))
 dedisperse_kernel(const uint8_t *__restrict__ xt, int64_t pitch, int32_t nchan, int32_t nchunks,
                   const int32_t *__restrict__ tile_first, const int32_t *__restrict__ tile_count,
                   const int4 *__restrict__ chunk_geo, const int32_t *__restrict__ chunk_off, int32_t copies_max,
                   int32_t raw_max, int64_t n_out, int32_t *__restrict__ out, int32_t *__restrict__ status) {
-    using S = Shape<CH, SPT>;
+    using S = Shape<CH, SPT, NDT>;
     extern __shared__ __align__(128) uint8_t smem[];
     int tile;
     int64_t tq;
     raster((int64_t)blockIdx.y * gridDim.x + blockIdx.x, (int)gridDim.x, (int64_t)gridDim.y, S::GROUP, tile, tq);
-    init_barriers<CH, SPT>(smem);
-    const bool ok = dedisp_tile<CH, SPT>(smem, 0u, xt, pitch, nchan, nchunks, tile_first[tile], tile_count[tile],
+    init_barriers(smem);
+    const bool ok = dedisp_tile<CH, SPT, NDT>(smem, 0u, xt, pitch, nchan, nchunks, tile_first[tile], tile_count[tile],
                                          tq * S::T, chunk_geo + (int64_t)tile * nchunks * CH,
                                          chunk_off + (int64_t)tile * nchunks * CH * S::DT, copies_max, raw_max,
                                          n_out, out);
@@ -439,12 +562,12 @@ __device__ __forceinline__ int beam_of(const int64_t *__restrict__ item_begin, i
 // beam by beam and, within a beam, in the raster order of the grid kernel;
 // beams may differ in length, DM list and channel count but share the kernel
 // shape.
-template <int CH, int SPT>
+template <int CH, int SPT, int NDT>
 __global__ void __launch_bounds__(CH * 32, (CH == 8 ? 2 : 3))
 dedisperse_items_kernel(const BatchBeamDev *__restrict__ beams, const int64_t *__restrict__ item_begin,
                         int32_t nbeams, int64_t nitems, int32_t copies_max, int32_t raw_max,
                         int32_t *__restrict__ status) {
-    using S = Shape<CH, SPT>;
+    using S = Shape<CH, SPT, NDT>;
     extern __shared__ __align__(128) uint8_t smem[];
     const int64_t item = blockIdx.x;
     if (item >= nitems) return;
@@ -453,8 +576,8 @@ dedisperse_items_kernel(const BatchBeamDev *__restrict__ beams, const int64_t *_
     int tile;
     int64_t tq;
     raster(item - __ldg(item_begin + b), bm.ntiles, (int64_t)bm.ntime, S::GROUP, tile, tq);
-    init_barriers<CH, SPT>(smem);
-    const bool ok = dedisp_tile<CH, SPT>(smem, 0u, bm.xt, bm.pitch, bm.nchan, bm.nchunks, __ldg(bm.tile_first + tile),
+    init_barriers(smem);
+    const bool ok = dedisp_tile<CH, SPT, NDT>(smem, 0u, bm.xt, bm.pitch, bm.nchan, bm.nchunks, __ldg(bm.tile_first + tile),
                                          __ldg(bm.tile_count + tile), tq * S::T,
                                          bm.geo + (int64_t)tile * bm.nchunks * CH,
                                          bm.off + (int64_t)tile * bm.nchunks * CH * S::DT, copies_max, raw_max,
@@ -466,15 +589,15 @@ dedisperse_items_kernel(const BatchBeamDev *__restrict__ beams, const int64_t *_
 // queue (one atomic per item) until it is empty; its mbarrier phases carry
 // over from item to item.  (counter == nullptr: one item per CTA, as the
 // items kernel, in this kernel's loop.)
-template <int CH, int SPT>
+template <int CH, int SPT, int NDT>
 __global__ void __launch_bounds__(CH * 32, (CH == 8 ? 2 : 3))
 dedisperse_batch_kernel(const BatchBeamDev *__restrict__ beams, const int64_t *__restrict__ item_begin,
                         int32_t nbeams, int64_t nitems, unsigned long long *__restrict__ counter,
                         int32_t copies_max, int32_t raw_max, int32_t *__restrict__ status) {
-    using S = Shape<CH, SPT>;
+    using S = Shape<CH, SPT, NDT>;
     extern __shared__ __align__(128) uint8_t smem[];
     long long *s_item = reinterpret_cast<long long *>(smem + kDedispItemOffset);
-    init_barriers<CH, SPT>(smem);
+    init_barriers(smem);
     uint32_t seq = 0;
     for (int pass = 0;; ++pass) {
         if (counter) {
@@ -491,7 +614,7 @@ dedisperse_batch_kernel(const BatchBeamDev *__restrict__ beams, const int64_t *_
         int tile;
         int64_t tq;
         raster(item - __ldg(item_begin + lo), bm.ntiles, (int64_t)bm.ntime, S::GROUP, tile, tq);
-        const bool ok = dedisp_tile<CH, SPT>(smem, seq, bm.xt, bm.pitch, bm.nchan, nchunks, __ldg(bm.tile_first + tile),
+        const bool ok = dedisp_tile<CH, SPT, NDT>(smem, seq, bm.xt, bm.pitch, bm.nchan, nchunks, __ldg(bm.tile_first + tile),
                                              __ldg(bm.tile_count + tile), tq * S::T,
                                              bm.geo + (int64_t)tile * nchunks * CH,
                                              bm.off + (int64_t)tile * nchunks * CH * S::DT, copies_max, raw_max,
@@ -516,17 +639,20 @@ struct ShapeKernels {
     int threads;
     int time_tile;
 };
-template <int CH, int SPT>
+template <int CH, int SPT, int NDT>
 constexpr ShapeKernels shape_kernels() {
-    return {dedisperse_kernel<CH, SPT>, dedisperse_batch_kernel<CH, SPT>, dedisperse_items_kernel<CH, SPT>, CH * 32,
-            Shape<CH, SPT>::T};
+    return {dedisperse_kernel<CH, SPT, NDT>, dedisperse_batch_kernel<CH, SPT, NDT>,
+            dedisperse_items_kernel<CH, SPT, NDT>, CH * 32, Shape<CH, SPT, NDT>::T};
 }
-static_assert(kDedispNumShapes == 3 && kDedispShapeCh[0] == 8 && kDedispShapeSpt[0] == 16 &&
-                  kDedispShapeCh[1] == 8 && kDedispShapeSpt[1] == 8 && kDedispShapeCh[2] == 4 &&
-                  kDedispShapeSpt[2] == 16,
+template <int I, int CH, int SPT, int NDT>
+constexpr bool shape_is() {
+    return kDedispShapeCh[I] == CH && kDedispShapeSpt[I] == SPT && kDedispShapeNdt[I] == NDT;
+}
+static_assert(kDedispNumShapes == 4 && shape_is<0, 8, 16, 8>() && shape_is<1, 8, 16, 4>() &&
+                  shape_is<2, 8, 8, 4>() && shape_is<3, 4, 16, 4>(),
               "compiled shapes match the shape table");
-const ShapeKernels kShapes[kDedispNumShapes] = {shape_kernels<8, 16>(), shape_kernels<8, 8>(),
-                                                shape_kernels<4, 16>()};
+const ShapeKernels kShapes[kDedispNumShapes] = {shape_kernels<8, 16, 8>(), shape_kernels<8, 16, 4>(),
+                                                shape_kernels<8, 8, 4>(), shape_kernels<4, 16, 4>()};
 
 constexpr int kMaxDev = 64;
 std::mutex g_cfg_lock;

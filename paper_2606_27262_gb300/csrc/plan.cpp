@@ -139,13 +139,17 @@ static int build_host_plan(const double *freqs_mhz, int32_t nchan, double tsamp_
     p->dms.assign(dms, dms + ndm);
     p->shape = shape;
     p->chan_chunk = kDedispShapeCh[shape];
-    p->dm_tile = kDedispDmPerThread * p->chan_chunk;
+    p->dm_tile = kDedispShapeNdt[shape] * p->chan_chunk;
     p->time_tile = 32 * kDedispShapeSpt[shape];
+    const int32_t max_span = kDedispShapeMaxSpan[shape];
+    const int32_t half_tile = 4 * p->chan_chunk;  // 4 DMs per thread
 
     // DM tiles: greedy runs of consecutive trial DMs (list order) with at
     // most dm_tile members and a per-channel delay spread (max - min over
-    // the run) of at most kDedispMaxSpan samples.  A single DM has spread 0,
-    // so every plan tiles.
+    // the run) of at most the shape's span.  A single DM has spread 0, so
+    // every plan tiles.  For a shape of 8 DMs per thread a run that cannot
+    // reach 3/4 of the tile is cut to 4 DMs per thread instead (a tile of
+    // 33..47 DMs would leave a quarter or more of its threads' DMs idle).
     std::vector<int32_t> lo(nchan), hi(nchan);
     int32_t d = 0;
     while (d < ndm) {
@@ -158,7 +162,7 @@ static int build_host_plan(const double *freqs_mhz, int32_t nchan, double tsamp_
             bool ok = true;
             for (int32_t c = 0; c < nchan && ok; ++c) {
                 const int32_t l = std::min(lo[c], r2[c]), h = std::max(hi[c], r2[c]);
-                ok = (h - l) <= kDedispMaxSpan;
+                ok = (h - l) <= max_span;
             }
             if (!ok) break;
             for (int32_t c = 0; c < nchan; ++c) {
@@ -167,6 +171,7 @@ static int build_host_plan(const double *freqs_mhz, int32_t nchan, double tsamp_
             }
             ++cnt;
         }
+        if (p->dm_tile > half_tile && cnt > half_tile && 4 * cnt < 3 * p->dm_tile) cnt = half_tile;
         p->tile_first.push_back(d);
         p->tile_count.push_back(cnt);
         d += cnt;
@@ -199,7 +204,7 @@ static int create_plan(const double *freqs_mhz, int32_t nchan, double tsamp_s, c
         delete p;
         return SP_ECUDA;
     }
-    if (p->smem_bytes > smem_optin) {  // cannot happen with the compiled shapes and kDedispMaxSpan
+    if (p->smem_bytes > smem_optin) {  // cannot happen with the compiled shapes and their spans
         delete p;
         return SP_ELIMIT;
     }
@@ -238,7 +243,7 @@ extern "C" int sp_plan_create_shaped(const double *freqs_mhz, int32_t nchan, dou
 
 extern "C" int sp_dedisp_shape_info(int32_t shape, int32_t *dm_tile, int32_t *time_tile, int32_t *chan_chunk) {
     if (shape < 0 || shape >= kDedispNumShapes) return SP_EINVAL;
-    if (dm_tile) *dm_tile = kDedispDmPerThread * kDedispShapeCh[shape];
+    if (dm_tile) *dm_tile = kDedispShapeNdt[shape] * kDedispShapeCh[shape];
     if (time_tile) *time_tile = 32 * kDedispShapeSpt[shape];
     if (chan_chunk) *chan_chunk = kDedispShapeCh[shape];
     return SP_OK;

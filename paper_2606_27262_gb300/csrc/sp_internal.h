@@ -12,18 +12,27 @@
 namespace sp {
 
 // Dedispersion tiling (see dedisperse.cu for the kernel these describe).
-// A kernel shape is (channels per chunk CH, samples per thread SPT): CH warps
-// of 4 trial DMs each, so a DM tile holds 4*CH DMs, and a time tile holds
-// 32*SPT output samples.  The shapes below are compiled; the autotuner picks
-// one per plan.
-constexpr int kDedispDmPerThread = 4;                     // trial DMs per thread
-constexpr int kDedispNumShapes = 3;
-constexpr int kDedispShapeCh[kDedispNumShapes] = {8, 8, 4};
-constexpr int kDedispShapeSpt[kDedispNumShapes] = {16, 8, 16};
+// A kernel shape is (channels per chunk CH, samples per thread SPT, trial
+// DMs per thread NDT): CH warps of NDT DMs each, so a DM tile holds up to
+// NDT*CH DMs, and a time tile holds 32*SPT output samples.  A shape with
+// NDT = 8 also runs tiles of at most 4*CH DMs with 4 DMs per thread.  The
+// shapes below are compiled; the autotuner picks one per plan.
+constexpr int kDedispNumShapes = 4;
+constexpr int kDedispShapeCh[kDedispNumShapes] = {8, 8, 8, 4};
+constexpr int kDedispShapeSpt[kDedispNumShapes] = {16, 16, 8, 16};
+constexpr int kDedispShapeNdt[kDedispNumShapes] = {8, 4, 4, 4};
+// Largest per-channel delay spread of a DM tile: for the 8-DM shape the
+// bound that keeps two CTAs' staging (8 windows of 512 + spread samples,
+// raw and as four shifted copies, plus a 64-DM offset table) in one SM's
+// shared memory.
+constexpr int kDedispShapeMaxSpan[kDedispNumShapes] = {680, 1024, 1024, 1024};
 constexpr int kDedispMaxChanChunk = 8;
 constexpr int kDedispMaxTimeTile = 512;                   // largest time tile of any shape
-constexpr int kDedispMaxSpan = 1024;                      // max delay spread in a DM tile
+constexpr int kDedispMaxSpan = 1024;                      // largest spread of any shape
 constexpr int kDedispTileGroupDms = 768;                  // DMs per raster group (24 tiles of 32)
+// 8-DM tiles keep 16-bit partial sums: at most 257 channels of bytes fit
+// a 16-bit lane, so the partials are added to the output every 256 channels.
+constexpr int kDedispPackedChannels = 256;
 // Shared-memory header of the dedispersion kernel: one mbarrier per raw
 // staging slot, then per slot the geometry and the (channel, DM) offset table
 // of the chunk it holds.
@@ -55,11 +64,11 @@ struct sp_plan {
     std::vector<double> freqs;    // host copy of the channel axis [nchan] (MHz)
     std::vector<double> dms;      // host copy of the trial DMs [ndm]
     std::vector<int32_t> delays;  // host copy [ndm][nchan]
-    // Kernel shape (index into kDedispShapeCh/Spt) and its tile sizes.
+    // Kernel shape (index into kDedispShapeCh/Spt/Ndt) and its tile sizes.
     int32_t shape = 0;
     int32_t dm_tile = 0, time_tile = 0, chan_chunk = 0;
     // DM tiles: consecutive runs of at most dm_tile trial DMs whose
-    // per-channel delay spread stays within kDedispMaxSpan.
+    // per-channel delay spread stays within the shape's maximum span.
     int32_t ntiles = 0;
     int32_t nchunks = 0;          // channel chunks of chan_chunk
     std::vector<int32_t> tile_first, tile_count;

@@ -95,10 +95,10 @@ def test_shape_table_and_batch_argument_checks(lib):
     seen = set()
     for s in range(sp.SP_DEDISP_NUM_SHAPES):
         assert lib.sp_dedisp_shape_info(s, ctypes.byref(dt), ctypes.byref(tt), ctypes.byref(cc)) == sp.SP_OK
-        assert dt.value == 4 * cc.value and tt.value % 128 == 0 and cc.value % 4 == 0
+        assert dt.value in (4 * cc.value, 8 * cc.value) and tt.value % 128 == 0 and cc.value % 4 == 0
         seen.add((dt.value, tt.value, cc.value))
     assert len(seen) == sp.SP_DEDISP_NUM_SHAPES
-    assert (32, 512, 8) in seen
+    assert (64, 512, 8) in seen and (32, 512, 8) in seen
     assert lib.sp_dedisp_shape_info(sp.SP_DEDISP_NUM_SHAPES, None, None, None) == sp.SP_EINVAL
     assert lib.sp_dedisp_shape_info(-1, None, None, None) == sp.SP_EINVAL
     f = synth.band_freqs(8)
@@ -158,7 +158,7 @@ def test_launch_counter_needs_no_device(lib):
     assert sp.launch_count() == c0
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
 def test_staging_tables_sound_for_every_workload(lib, shape):
     """Every bulk copy, shifted copy and shared load the dedispersion kernel
     makes with a plan's tables stays aligned and in bounds (host-only check),

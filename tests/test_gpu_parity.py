@@ -224,6 +224,44 @@ def test_searcher_run_host_matches_device_path():
     assert np.array_equal(sp.cands_to_numpy(dc.cpu().numpy(), n), want)
 
 
+def test_searcher_pipelined_host_runs_match_run_host():
+    """submit_host/collect on three different beams in a row (two in flight)
+    gives each beam the result run_host gives it; a third submit with two
+    uncollected beams and a collect with none queued are refused."""
+    wl = synth.config1()
+    plan = sp.Plan(wl.freqs, wl.tsamp, wl.dms)
+    n_in = wl.n_out + plan.max_delay
+    s = sp.Searcher(plan, wl.n_out, wl.widths, wl.threshold, wl.norm_block, 1 << 16)
+    beams = [torch.from_numpy(synth.make_workload_beam(wl, n_in, seed=seed)[0]).pin_memory() for seed in (5, 6, 7)]
+    want = []
+    for b in beams:
+        hc = np.zeros((1 << 16, 4), np.int32)
+        n = s.run_host(b, hc)
+        want.append(sp.cands_to_numpy(hc, n))
+    got = []
+    s.submit_host(beams[0])
+    s.submit_host(beams[1])
+    with pytest.raises(sp.SpotlightError):
+        s.submit_host(beams[2])
+    for k in range(3):
+        hc = np.zeros((1 << 16, 4), np.int32)
+        n = s.collect(hc)
+        got.append(sp.cands_to_numpy(hc, n))
+        if k == 0:
+            s.submit_host(beams[2])
+    with pytest.raises(sp.SpotlightError):
+        s.collect(np.zeros((4, 4), np.int32))
+    for g, w in zip(got, want):
+        assert g.size > 0 and np.array_equal(g, w)
+    # a smaller caller capacity: five of the candidates, and the full count
+    s.submit_host(beams[0])
+    hc = np.zeros((5, 4), np.int32)
+    assert s.collect(hc) == want[0].size
+    full = {(int(a), int(b)) for a, b in zip(want[0]["dm_idx"], want[0]["t"])}
+    part = sp.cands_to_numpy(hc, 5)
+    assert part.size == 5 and all((int(a), int(b)) in full for a, b in zip(part["dm_idx"], part["t"]))
+
+
 @pytest.fixture(scope="module")
 def config2_run():
     wl = synth.config2()

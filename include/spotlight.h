@@ -101,6 +101,16 @@ int sp_plan_info(const sp_plan *plan, int32_t *max_delay, int32_t *nchan, int32_
  * Reads it after synchronising the device; clear != 0 resets it. */
 #define SP_STATUS_STAGING_TIMEOUT 1
 int sp_plan_status(const sp_plan *plan, int32_t *h_status, int32_t clear);
+/* Test hook of the failure path above (the paper has no counterpart): on
+ * the current device, every later dedispersion CTA's first chunk expects
+ * extra_bytes (a multiple of 16, <= 1 MiB) more than its bulk copies bring,
+ * and every staging wait gives up after wait_limit_cycles SM cycles (>=
+ * 1024).  With extra_bytes > 0 the first wait of every CTA runs out, the CTA
+ * waits once more (bounded) and leaves, and the status word gets
+ * SP_STATUS_STAGING_TIMEOUT; no access leaves its buffers and the device
+ * stays usable.  sp_debug_staging_fault(0, 1LL << 31) restores the
+ * defaults.  Not for use while dedispersion kernels are in flight. */
+int sp_debug_staging_fault(int32_t extra_bytes, int64_t wait_limit_cycles);
 /* Copies the delay table, int32 [ndm][nchan], to host memory. */
 int sp_plan_delays(const sp_plan *plan, int32_t *h_out);
 /* The same delay table computed on the host only (no device, no plan):

@@ -34,6 +34,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libspotlight.so")
 
 SP_OK, SP_EINVAL, SP_ESHAPE, SP_ECUDA, SP_EOVERFLOW, SP_ENOMEM, SP_EWORKSPACE, SP_ELIMIT = 0, -1, -2, -3, -4, -5, -6, -7
 SP_ETIMEOUT = -8
+SP_STATUS_STAGING_TIMEOUT = 1
 SP_MAX_WIDTHS = 16
 SP_MAX_WIDTH = 1024
 
@@ -74,6 +75,7 @@ SIGNATURES = {
     "sp_searcher_run": (ctypes.c_int, [P, P, P, I64, P, P]),
     "sp_searcher_run_host": (ctypes.c_int, [P, P, P, I64, P, P]),
     "sp_searcher_submit_host": (ctypes.c_int, [P, P, P]),
+    "sp_debug_staging_fault": (ctypes.c_int, [ctypes.c_int32, I64]),
     "sp_searcher_collect": (ctypes.c_int, [P, P, I64, P]),
     "sp_dedisp_shape_info": (ctypes.c_int, [I32, P, P, P]),
     "sp_plan_create_shaped": (ctypes.c_int, [P, I32, F64, P, I32, I32, P]),
@@ -389,6 +391,13 @@ class Searcher:
             self.close()
         except Exception:
             pass
+
+
+def debug_staging_fault(extra_bytes: int, wait_limit_cycles: int = 1 << 31):
+    """Test hook: make every dedispersion CTA's first staging wait expect
+    extra_bytes more than arrive, with waits bounded at wait_limit_cycles
+    (sp_debug_staging_fault); (0, 1 << 31) restores the defaults."""
+    _check(_lib().sp_debug_staging_fault(int(extra_bytes), int(wait_limit_cycles)), "sp_debug_staging_fault")
 
 
 def autotune_dedisperse(freqs_mhz, tsamp_s: float, dms, n_out_sample: int = SP_AUTOTUNE_SAMPLES,

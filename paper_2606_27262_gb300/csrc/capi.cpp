@@ -96,6 +96,13 @@ extern "C" const char *sp_strerror(int code) {
     }
 }
 
+extern "C" int sp_debug_staging_fault(int32_t extra_bytes, int64_t wait_limit_cycles) {
+    if (extra_bytes < 0 || (extra_bytes & 15) || extra_bytes > (1 << 20) || wait_limit_cycles < 1024 ||
+        wait_limit_cycles > (1LL << 40))
+        return SP_EINVAL;
+    return set_staging_fault((uint32_t)extra_bytes, (long long)wait_limit_cycles);
+}
+
 extern "C" int64_t sp_staged_pitch(int64_t n_in) { return n_in > 0 ? dedisp_pitch(n_in) : -1; }
 
 extern "C" int64_t sp_staged_bytes(int32_t nchan, int64_t n_in) {

@@ -115,12 +115,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// Bounded wait: gives up after ~2^31 SM cycles (about a second).
+// Test hook of the bounded waits (sp_debug_staging_fault): the number of
+// SM cycles after which a staging wait gives up (~2^31, about a second, by
+// default), and extra bytes that every CTA's first chunk expects beyond
+// those its bulk copies bring (0 by default), so that a test can make the
+// waits run out with every access in bounds.
+__device__ long long g_wait_limit = 1LL << 31;
+__device__ uint32_t g_fault_extra_bytes = 0;
+
+// Bounded wait: gives up after g_wait_limit SM cycles.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
+    const long long limit = *(volatile long long *)&g_wait_limit;
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -253,7 +262,8 @@ __device__ __forceinline__ bool dedisp_tile_body(uint8_t *smem, uint32_t seq0, c
         for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
         if (lane < CH) geo_s[sl * CH + lane] = (lane < nc) ? g : zero4;
         fence_proxy_async();
-        if (lane == 0) mbar_arrive_expect_tx(&mbar[sl], bytes + (uint32_t)(CH * DT * 4));
+        if (lane == 0)
+            mbar_arrive_expect_tx(&mbar[sl], bytes + (uint32_t)(CH * DT * 4) + (kk == 0 ? g_fault_extra_bytes : 0u));
         __syncwarp();
         if (lane < nc)
             bulk_g2s(raw_s + sl * raw_max + g.w, xt + (int64_t)(kk * CH + lane) * pitch + t0 + g.x,
@@ -678,6 +688,15 @@ int configure_shape(int shape, int smem_bytes) {
 }
 
 }  // namespace
+
+int set_staging_fault(uint32_t extra_bytes, long long wait_limit) {
+    if (cudaMemcpyToSymbol(g_fault_extra_bytes, &extra_bytes, sizeof extra_bytes) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_wait_limit, &wait_limit, sizeof wait_limit) != cudaSuccess) {
+        cudaGetLastError();
+        return SP_ECUDA;
+    }
+    return SP_OK;
+}
 
 int launch_stage_input(const uint8_t *d_in, int64_t n_in, int32_t nchan, uint8_t *d_staged, int64_t pitch,
                        cudaStream_t stream, int64_t row0, int64_t ring_rows) {

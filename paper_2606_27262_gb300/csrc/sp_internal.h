@@ -132,6 +132,8 @@ int batch_grid(BatchLaunch &b);
 // persistent: a resident grid draining the work queue; else one CTA per item.
 int launch_dedisperse_batch(const BatchLaunch &b, cudaStream_t stream, bool persistent = true);
 int64_t dedisp_time_tiles(const sp_plan *plan, int64_t n_out);
+// Test hook of the dedispersion kernel's bounded waits on the current device.
+int set_staging_fault(uint32_t extra_bytes, long long wait_limit);
 // Sets the dynamic shared-memory limit of the plan's kernels on the current
 // device (once per device and size); called before any launch or capture.
 int dedisp_configure(const sp_plan *plan);

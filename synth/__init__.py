@@ -205,18 +205,25 @@ def make_beam(seed: int, nchan: int, n_in: int, freqs: np.ndarray, bursts: list[
 
 
 def make_beam_torch(seed: int, out, freqs: np.ndarray, bursts: list[Burst] | None = None, widths=(1,),
-                    gains: np.ndarray | None = None, tsamp: float = TSAMP, chunk_rows: int = 16384):
+                    gains: np.ndarray | None = None, tsamp: float = TSAMP, chunk_rows: int = 16384,
+                    extra=None):
     """The noise model of ``make_beam`` drawn on a torch device (for beams
     too large to draw on the host in reasonable time): fills ``out``, a
     uint8 tensor [n_in][nchan], in place.  Same distribution and burst
     model; a different random stream (torch's generator, seeded by
-    ``seed``)."""
+    ``seed``).  ``extra``: another sparse signal (rows, cols, values), e.g.
+    RFI from ``synth.rfi.rfi_signal``, added before the gain and rounding."""
     import torch
     n_in, nchan = int(out.shape[0]), int(out.shape[1])
     dev = out.device
     freqs = np.asarray(freqs, dtype=np.float64)
     g = np.ones(nchan, np.float64) if gains is None else np.asarray(gains, np.float64)
     sr, sc, sv = _burst_signal(list(bursts or []), freqs, n_in, widths, g, tsamp)
+    if extra is not None and len(extra[0]):
+        sr, sc, sv = (np.concatenate([sr, extra[0]]), np.concatenate([sc, extra[1]]),
+                      np.concatenate([sv, extra[2]]))
+        order = np.argsort(sr, kind="stable")
+        sr, sc, sv = sr[order], sc[order], sv[order]
     gen = torch.Generator(device=dev)
     gen.manual_seed(int(seed))
     gt = torch.as_tensor(g.astype(np.float32), device=dev)

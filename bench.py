@@ -13,8 +13,11 @@ so no L2 flush is needed between steps.
           (input staging + dedispersion + block statistics + boxcar/peaks + the 64-bit
           boxcar pass over tiles the 32-bit pass could not prove exact), inputs
           resident in HBM.
-  e2e     the same metric through sp_searcher_run_host: pinned host input
-          copied in, candidates copied out, every step.
+  e2e     the same metric through the searcher's host API: every step copies
+          its pinned host input in and its candidates out; beams go back to
+          back (sp_searcher_submit_host / sp_searcher_collect, two in flight,
+          so each input copy overlaps the previous beam's search), with the
+          one-beam-at-a-time sp_searcher_run_host figure beside it.
   roofline  dedispersion kernel alone: channel x DM x sample adds per launch
           over its CUDA-event time, against the integer-add issue rate
           (SMs x measured 32-bit add lanes per SM per clock x max SM clock).
@@ -37,11 +40,14 @@ per second, next to the same work as per-beam launches (also a graph).
 channels arriving as 8.0 s gulps (6104 samples) overlapped by the DM-2000
 sweep (5751 trials), device rings and slots admitted by an HBM budget,
 continuous batching, each gulp's candidates sifted on the host and the kept
-peaks scored by the classifier inside the stream.  value = sustained
-real-time beams (gulps finished per second at saturation x 8.0 s), next to
-the same stream without sifter and classifier and to per-gulp launches on
-one stream with the plain sifter; the p50/p99 latency of real-time arrivals
-for the 256 beams through the whole chain is reported against the 8.0 s
+peaks scored by the classifier inside the stream.  The classifier is first
+trained in the run by the library's own kernels (synthetic subband spectra,
+then the kept peaks of beams with injected bursts and RFI).  value =
+sustained real-time beams (gulps finished per second at saturation x 8.0 s),
+next to the same stream without sifter and classifier and to per-gulp
+launches on one stream with the plain sifter; the chain's recall on bursts
+injected into streamed beams; the p50/p99 latency of real-time arrivals at
+90 % of the sustained rate through the whole chain against the 8.0 s
 deadline.
 
 `--workload classifier` measures the candidate classifier: training steps
@@ -91,6 +97,10 @@ def parse_args(argv=None):
     p.add_argument("--stream-beams", type=int, default=256, help="stream workload: beams")
     p.add_argument("--stream-periods", type=float, default=3.0,
                    help="stream workload: gulp periods of real-time arrivals for the latency figures")
+    p.add_argument("--stream-train-beams", type=int, default=96,
+                   help="stream workload: beams with bursts and RFI whose kept peaks train the classifier")
+    p.add_argument("--stream-recall-beams", type=int, default=32,
+                   help="stream workload: streamed beams carrying injected bursts for the chain's recall")
     p.add_argument("--stream-plan", choices=["dm2000", "dm500"], default="dm2000",
                    help="stream workload: the 5751-trial plan to DM 2000 or the 501-trial plan to DM 500")
     p.add_argument("--beams", type=int, default=128, help="batched workload: number of beams")
@@ -569,6 +579,108 @@ def run_batched(args):
 
 
 # ----------------------------------------------------------------- stream --
+def train_pipeline_classifier(plan, freqs, widths, dev, seed: int, nbeams: int):
+    """The classifier trained by the library's kernels: 2000 steps of 64
+    synthetic subband spectra (60 % bursts), then 1500 steps of 64 kept peaks
+    (half on bursts) of ``nbeams`` 16384-sample beams with 4 injected bursts
+    (DM 50-1950, FWHM 1-64 samples, S/N 6-50) and 3-6 RFI events each, found
+    by this plan's search and the sifter.  Returns (classifier, info)."""
+    import numpy as np
+    import torch
+
+    import paper_2606_27262_gb300 as sp
+    from paper_2606_27262_gb300 import learning
+    from synth import classifier as scls
+    from synth import rfi
+    n_out = 16384
+    h = learning.Harvester(plan, n_out, widths, 6.0, 8192, device=dev)
+    beam = torch.empty((n_out + plan.max_delay, plan.nchan), dtype=torch.uint8, device=dev)
+
+    def make(sd, out):
+        return [learning.Truth(b.t0, b.dm, b.fwhm, b.snr) for b in rfi.pipeline_beam(sd, out, freqs, n_out, widths)]
+    hv = learning.harvest_beams(h, make, range(seed, seed + nbeams), beam)
+    del h, beam
+    clf = sp.Classifier(max_batch=64, seed=seed)
+    rng = np.random.default_rng(seed)
+
+    def sample(n):
+        sub, labels, _ = scls.classifier_batch(rng, n, freqs, device=dev, t_in=512, p_burst=0.6)
+        return sub, labels
+    pre = learning.train(clf, learning.subband_batches(sample, freqs, 64, device=dev), 2000)
+    post = learning.train(clf, learning.pool_batches(hv.ft, hv.dm_img, hv.labels, rng, 64), 1500, lr=1e-3)
+    info = {"synthetic_steps": 2000, "pipeline_steps": 1500, "batch": 64, "pipeline_beams": nbeams,
+            "pipeline_kept_peaks": int(hv.labels.size), "pipeline_burst_peaks": int(hv.labels.sum()),
+            "loss_first": pre[0], "loss_last": post[-1]}
+    return clf, info
+
+
+def stream_recall(plan, clf, freqs, widths, gulp: int, cap: int, kept_cap: int, t_in: int, dev, seed: int,
+                  nbeams: int):
+    """Streams ``nbeams`` beams whose first max_delay samples (the history
+    that the first searched windows cover) hold one dispersed burst per
+    gulp-long window (S/N 8-30, FWHM 1-16 samples, DM 50-1000 with the sweep
+    inside the history) and 4 RFI events, through search, sifter and the
+    classifier; the pushed gulps are noise.  A burst counts as kept when the
+    sifter keeps a peak on it and as accepted when the classifier accepts one
+    of those peaks."""
+    import numpy as np
+    import torch
+
+    import paper_2606_27262_gb300 as sp
+    import synth
+    from paper_2606_27262_gb300 import learning
+    from synth import rfi
+    nchan, D = plan.nchan, plan.max_delay
+    rounds = D // gulp
+    per_dm = float(synth.fractional_delay(freqs, 1.0)[-1])
+    s = sp.Stream(plan, nbeams, gulp, widths, 6.0, 8192, cap, 24 * (1 << 30) + nbeams * (gulp + D) * nchan,
+                  max_batch=16)
+    s.attach(clf, t_in=t_in, kept_cap=kept_cap)
+    hist_d = torch.empty((D, nchan), dtype=torch.uint8, device=dev)
+    truths = []
+    for b in range(nbeams):
+        rng = np.random.default_rng((seed, b))
+        bursts = []
+        for k in range(rounds):
+            t0 = k * gulp + int(rng.integers(64, gulp - 64))
+            fwhm = float(rng.uniform(1.0, 16.0))
+            dm_hi = min(1000.0, (D - t0 - 8 * fwhm - 64) / per_dm)
+            if dm_hi < 60.0:
+                break
+            bursts.append(synth.Burst(t0, float(rng.uniform(50.0, dm_hi)), fwhm, float(rng.uniform(8.0, 30.0))))
+        events = rfi.draw_rfi(rng, 4, D, nchan)
+        synth.make_beam_torch(seed * 1000 + b, hist_d, freqs, bursts, widths=widths,
+                              extra=rfi.rfi_signal(events, D, nchan))
+        s.history(b, np.ascontiguousarray(hist_d.cpu().numpy()))
+        truths.append(bursts)
+    noise = [torch.from_numpy(synth.make_beam((seed, 50 + i), nchan, gulp, freqs)).pin_memory() for i in range(4)]
+    for k in range(rounds):
+        for b in range(nbeams):
+            s.push(b, noise[(b + k) % len(noise)])
+    res = s.drain(with_cands=False, sifted=True)
+    s.close()
+    kept_b = acc_b = injected = fp_sifter = fp_clf = overflow = 0
+    for info, _, kept, prob in res:
+        k = int(info.seq)
+        win = [learning.Truth(bb.t0 - k * gulp, bb.dm, bb.fwhm, bb.snr) for bb in truths[int(info.beam)]
+               if k * gulp <= bb.t0 < (k + 1) * gulp]
+        which = learning.match_peaks(kept, plan.dms, widths, win)
+        overflow += int(info.kept) > kept_cap
+        for i in range(len(win)):
+            injected += 1
+            on = which == i
+            if on.any():
+                kept_b += 1
+                acc_b += bool((prob[on] >= 0.5).any())
+        fp_sifter += int((which < 0).sum())
+        fp_clf += int(((which < 0) & (prob >= 0.5)).sum())
+    return {"beams": nbeams, "gulps": len(res), "bursts_injected": injected, "bursts_kept_by_sifter": kept_b,
+            "bursts_accepted": acc_b, "recall_vs_sifter": acc_b / max(kept_b, 1),
+            "recall_vs_injected": acc_b / max(injected, 1), "snr_range": [8.0, 30.0],
+            "non_burst_peaks_sifter": fp_sifter, "non_burst_peaks_accepted": fp_clf,
+            "gulps_over_kept_cap": overflow}
+
+
 def run_stream(args):
     import numpy as np
     import torch
@@ -623,10 +735,14 @@ def run_stream(args):
     budget = int(args.dmt_budget_gb * (1 << 30)) + nbeams * (gulp + plan.max_delay) * nchan
     adds_per_gulp = float(nchan) * plan.ndm * gulp
 
-    # The classifier of the full chain: random-init weights (its cost does
-    # not depend on them; the trained network's recall is a test result).
-    clf = sp.Classifier(max_batch=64, seed=5)
+    # The classifier of the full chain, trained here by the library's own
+    # kernels: synthetic subband spectra first, then the kept peaks of beams
+    # with injected bursts and RFI searched by this plan.
     t_in, kept_cap = 512, 64
+    t_train = time.perf_counter()
+    clf, train_info = train_pipeline_classifier(plan, freqs, widths, dev, 3005 + 101 * rank,
+                                                args.stream_train_beams)
+    train_info["seconds"] = time.perf_counter() - t_train
 
     def make_stream(flags, max_batch, stage):
         s = sp.Stream(plan, nbeams, gulp, widths, 6.0, 8192, cap, budget, max_batch=max_batch, flags=flags)
@@ -675,13 +791,28 @@ def run_stream(args):
     rate_p, dt_p, info_p = saturated(sp.SP_STREAM_PER_GULP | sp.SP_STREAM_ONE_STREAM, 1, "sift")
     rate_q, dt_q, info_q = saturated(sp.SP_STREAM_PER_GULP | sp.SP_STREAM_ONE_STREAM, 1, None)
 
-    # Real-time arrivals: every beam pushes a gulp each period, beams
-    # staggered evenly over the period; the full chain (search, sifter,
-    # classifier) is attached.
-    s = make_stream(0, 16, "classify")
+    # Recall of the whole chain (search, sifter, classifier) on bursts
+    # injected into the streamed beams themselves.
+    recall = stream_recall(plan, clf, freqs, widths, gulp, cap, kept_cap, t_in, dev, 2007 + 31 * rank,
+                           args.stream_recall_beams)
+
+    # Real-time arrivals near saturation: as many beams as 90 % of the
+    # sustained rate above serves (fewer if their rings do not fit the
+    # device), every beam pushing a gulp each period, beams staggered evenly
+    # over the period; the full chain attached.
+    ring_bytes = (gulp + plan.max_delay) * nchan
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info(dev)
+    fit = int((free - 40 * (1 << 30)) // ring_bytes)
+    nb_rt = max(1, min(int(0.9 * rate_b * period), fit))
+    s = sp.Stream(plan, nb_rt, gulp, widths, 6.0, 8192, cap,
+                  int(args.dmt_budget_gb * (1 << 30)) + nb_rt * ring_bytes, max_batch=16)
+    s.attach(clf, t_in=t_in, kept_cap=kept_cap)
+    for b in range(nb_rt):
+        s.history(b, hist)
     lat, lat_search, cand_total, kept_total = [], [], 0, 0
     nper = max(1, int(round(args.stream_periods)))
-    arrivals = sorted((k * period + b * period / nbeams, b, k) for k in range(nper) for b in range(nbeams))
+    arrivals = sorted((k * period + b * period / nb_rt, b, k) for k in range(nper) for b in range(nb_rt))
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     t_start = sp.stream_now() + 0.05
@@ -717,7 +848,7 @@ def run_stream(args):
                    "chain": f"batched dedispersion (one CTA per work item while a classifier is attached), "
                             f"search on a high-priority stream, host DBSCAN sifter (Sec. 3.2.1 defaults), "
                             f"classifier on the kept peaks of each finished batch on a high-priority stream "
-                            f"(t_in {t_in}, up to {kept_cap} per gulp, random-init weights: throughput only)",
+                            f"(t_in {t_in}, up to {kept_cap} per gulp, weights trained in this run)",
                    "l2": "rings and windows larger than L2, no flush", "parallelism": f"replicas x{world}"},
         "sifted": {"candidates": info_b["candidates"], "kept": info_b["kept"], "classified": info_b["kept"],
                    "gulps": 2 * nbeams},
@@ -730,7 +861,10 @@ def run_stream(args):
         "per_gulp_search_only": {"value": world * rate_q * period, "unit": "beams", "ms_per_gulp": 1e3 / rate_q,
                                  "launches": "as per_gulp, without the sifter"},
         "speedup_vs_per_gulp": rate_b / rate_p,
-        "latency": {"beams": nbeams, "periods": nper, "gulps": int(lat.size), "deadline_s": period,
+        "classifier_training": train_info,
+        "recall": recall,
+        "latency": {"beams": nb_rt, "load_vs_sustained": nb_rt / (rate_b * period), "periods": nper,
+                    "gulps": int(lat.size), "deadline_s": period,
                     "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                     "max_s": float(lat.max()), "met_deadline": bool(lat.max() < period),
                     "search_p50_s": float(np.percentile(lat_search, 50)),

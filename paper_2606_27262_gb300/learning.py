@@ -158,3 +158,54 @@ def pool_batches(ft, dm_img, labels: np.ndarray, rng, batch: int, p_pos: float =
         it = torch.from_numpy(idx).to(ft.device)
         return ft.index_select(0, it).contiguous(), dm_img.index_select(0, it).contiguous(), lab_d.index_select(0, it)
     return fn
+
+
+@dataclasses.dataclass
+class Harvest:
+    """Kept peaks of many beams: images, labels, and per beam the peaks,
+    the burst each lies on (-1: none) and the injected bursts."""
+    ft: object
+    dm_img: object
+    labels: np.ndarray
+    beams: list
+    candidates: int
+
+
+def harvest_beams(h: Harvester, make_beam, seeds, beam) -> Harvest:
+    """Runs ``h`` on the beam make_beam(seed, beam) -> truths writes into the
+    device tensor ``beam`` for every seed."""
+    import torch
+    fts, dms, labs, beams, n_cands = [], [], [], [], 0
+    for s in seeds:
+        truths = make_beam(s, beam)
+        ft, dm_img, lab, kept, which, n = h.run(beam, truths)
+        fts.append(ft)
+        dms.append(dm_img)
+        labs.append(lab)
+        beams.append((kept, which, truths))
+        n_cands += n
+    return Harvest(torch.cat(fts), torch.cat(dms), np.concatenate(labs), beams, n_cands)
+
+
+def judge(p: np.ndarray, hv: Harvest, snr_min: float = 8.0, p_min: float = 0.5) -> dict:
+    """Recall and false positives of probabilities p (one per kept peak of
+    ``hv``): a burst injected at S/N >= snr_min counts as kept when the
+    sifter kept a peak on it, and as accepted when one of those peaks has
+    p >= p_min; non-burst peaks are the sifter's false positives."""
+    kept_b = acc_b = injected = 0
+    off = 0
+    for kept, which, truths in hv.beams:
+        pb = p[off:off + kept.size]
+        off += kept.size
+        for i, tr in enumerate(truths):
+            if tr.snr < snr_min:
+                continue
+            injected += 1
+            on = which == i
+            if on.any():
+                kept_b += 1
+                acc_b += bool((pb[on] >= p_min).any())
+    noise = hv.labels == 0
+    return {"injected": injected, "kept": kept_b, "accepted": acc_b, "recall": acc_b / max(kept_b, 1),
+            "fp_sifter": int(noise.sum()), "fp_classifier": int((p[noise] >= p_min).sum()),
+            "kept_peaks": int(hv.labels.size), "candidates": int(hv.candidates)}

@@ -96,3 +96,20 @@ def rfi_signal(events: list[Rfi], n_in: int, nchan: int):
         z = np.zeros(0, np.int64)
         return z, z, np.zeros(0)
     return np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+
+
+def pipeline_beam(seed: int, out, freqs, n_out: int, widths, nbursts: int = 4, dm_lo: float = 50.0,
+                  dm_hi: float = 1950.0, fwhm_lo: float = 1.0, fwhm_hi: float = 64.0, snr_lo: float = 6.0,
+                  snr_hi: float = 50.0, nrfi_lo: int = 3, nrfi_hi: int = 6):
+    """A beam for training and judging the classifier on the search's own
+    candidates: fills ``out`` (uint8 CUDA tensor [n_in][nchan], n_in >=
+    n_out + the sweep of dm_hi) with noise, ``nbursts`` dispersed bursts
+    arriving in [64, n_out) and 3-6 RFI events anywhere in the input.
+    Returns the bursts (amplitudes filled in)."""
+    from . import draw_bursts, make_beam_torch
+    rng = np.random.default_rng((seed, 7))
+    bursts = draw_bursts(rng, nbursts, n_out, dm_lo, dm_hi, fwhm_lo, fwhm_hi, snr_lo, snr_hi)
+    n_in, nchan = int(out.shape[0]), int(out.shape[1])
+    events = draw_rfi(rng, int(rng.integers(nrfi_lo, nrfi_hi + 1)), n_in, nchan)
+    make_beam_torch(seed, out, freqs, bursts, widths=widths, extra=rfi_signal(events, n_in, nchan))
+    return bursts

@@ -997,7 +997,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
+    import numpy as np
 
     import oracle
     import synth
@@ -1008,17 +1008,25 @@ def run_reference(args):
     beam_s = wl.n_out * wl.tsamp
     for _ in range(max(args.warmup, 0)):
         cpu_oracle_sample(wl, delays, x, args.cpu_stride * 4)
+    # A step is the bounded sample itself (every stride-th trial DM of the
+    # beam, full length): ms_per_step is the time it took, and the value
+    # scales the sampled share of the beam's data to real-time beams.
     times, desc, cores = [], "", oracle.num_threads()
+    ndm = delays.shape[0]
+    frac = np.arange(0, ndm, args.cpu_stride).size / ndm
     for _ in range(args.steps):
         full_s, desc, cores = cpu_oracle_sample(wl, delays, x, args.cpu_stride)
-        times.append(full_s)
-    ms_step = statistics.mean(times) * 1e3
-    value = beam_s / (ms_step / 1e3)
+        times.append(full_s * frac)
+    sample_s = statistics.mean(times)
+    value = beam_s * frac / sample_s
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "beams", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sample_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": config_dict(wl, delays.shape[0], int(delays.max())) | {"parallelism": "host cores"},
+        "config": config_dict(wl, ndm, int(delays.max())) | {"parallelism": "host cores"},
+        "step": f"one sampled step: every {args.cpu_stride}th trial DM ({round(frac * ndm)} of {ndm}) of one beam "
+                f"at full length; value = the sampled share of the beam's {beam_s:.1f} s of data per second",
+        "extrapolated": True, "trial_fraction": frac, "full_beam_s_extrapolated": sample_s / frac,
         "cpu_baseline": {"value": value, "unit": "beams", "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "beams", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

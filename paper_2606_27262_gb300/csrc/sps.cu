@@ -244,7 +244,17 @@ __device__ __forceinline__ int64_t block_of(int64_t t, int64_t norm_block, int64
 // one staged row: best S/N over the widths and its width index.
 // `interior`: every point of the tile is a sample of the beam; `tile_block`:
 // the one normalisation block of all of them, or -1.
-template <typename PT, int NP>
+// MAGIC (32-bit pass, every |S - w*m0| of the tile below 2^22): the
+// integer converts to float by adding the bit pattern of 1.5*2^23 and
+// subtracting that float (exact below 2^22), and on the check-free path the
+// best width is kept with one float max: the width code 15 - k sits in the
+// low 4 mantissa bits of the S/N (on equal upper bits the smaller width
+// wins), cleared again when the point is stored.  The S/N keeps 19 bits:
+// within 2^-19 relative of the value the exact compare would keep.
+constexpr uint32_t kMagicBits = 0x4B400000u;   // bit pattern of 12582912.0f = 1.5 * 2^23
+constexpr float kMagicValue = 12582912.0f;
+
+template <typename PT, int NP, bool MAGIC>
 __device__ __forceinline__ void score_points(const PT *Q, int d, int64_t s0, int64_t n_out, int fit_end, int p0,
                                              bool interior, int64_t tile_block, const WidthList &wl,
                                              int64_t norm_block, int64_t nblk, const int32_t *__restrict__ m0s,
@@ -280,19 +290,41 @@ __device__ __forceinline__ void score_points(const PT *Q, int d, int64_t s0, int
             PT q0[NP];
 #pragma unroll
             for (int j = 0; j < NP; ++j) q0[j] = Q[kBxFirst + p0 + 16 * j - 1];
-            for (int k = 0; k < wl.nw; ++k) {
-                const int w = wl.w[k];
-                const PT cw = (PT)w * m0;
-                const float2 cf = __ldg(cfs + k);
-                const PT *Qw = Q + kBxFirst + p0 + w - 1;
+            if constexpr (MAGIC) {
+                for (int k = 0; k < wl.nw; ++k) {
+                    const int w = wl.w[k];
+                    const uint32_t mc = kMagicBits - (uint32_t)w * (uint32_t)m0;
+                    const float2 cf = __ldg(cfs + k);
+                    const PT *Qw = Q + kBxFirst + p0 + w - 1;
+                    const uint32_t code = 15u - (uint32_t)k;
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        const uint32_t xs = (uint32_t)Qw[16 * j] - (uint32_t)q0[j] + mc;
+                        const float sv = fmaf(__uint_as_float(xs) - kMagicValue, cf.x, -cf.y);
+                        best[j] = fmaxf(best[j], __uint_as_float((__float_as_uint(sv) & ~15u) | code));
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
-                    const PT xs = Qw[16 * j] - q0[j] - cw;
-                    const float xf = sizeof(PT) == 4 ? (float)(int32_t)xs : (float)(int64_t)xs;
-                    const float sv = fmaf(xf, cf.x, -cf.y);
-                    if (sv > best[j]) {
-                        best[j] = sv;
-                        kb[j] = k;
+                    const uint32_t bits = __float_as_uint(best[j]);
+                    kb[j] = 15 - (int)(bits & 15u);
+                    best[j] = __uint_as_float(bits & ~15u);
+                }
+            } else {
+                for (int k = 0; k < wl.nw; ++k) {
+                    const int w = wl.w[k];
+                    const PT cw = (PT)w * m0;
+                    const float2 cf = __ldg(cfs + k);
+                    const PT *Qw = Q + kBxFirst + p0 + w - 1;
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        const PT xs = Qw[16 * j] - q0[j] - cw;
+                        const float xf = sizeof(PT) == 4 ? (float)(int32_t)xs : (float)(int64_t)xs;
+                        const float sv = fmaf(xf, cf.x, -cf.y);
+                        if (sv > best[j]) {
+                            best[j] = sv;
+                            kb[j] = k;
+                        }
                     }
                 }
             }
@@ -395,7 +427,7 @@ __device__ __forceinline__ bool boxcar_tile(const BoxcarArgs &a, int tx, int ty,
     const int64_t be = ts <= te ? block_of(te, a.norm_block, a.nblk) : -1;
     const int64_t tile_block = bs == be ? bs : -1;
 
-    bool wide = false;
+    bool wide = false, big = sizeof(PT) != 4;
     for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
         const int d = d0 - 1 + rr;
         if (d < 0 || d >= a.ndm) continue;
@@ -413,12 +445,14 @@ __device__ __forceinline__ bool boxcar_tile(const BoxcarArgs &a, int tx, int ty,
                         const int64_t m0 = __ldg(a.m0s + (int64_t)d * a.nblk + b);
                         const int64_t dev = max((int64_t)vmax - m0, m0 - (int64_t)vmin);
                         if (dev * a.maxw > (int64_t)INT32_MAX) wide = true;
+                        if (dev * a.maxw >= (int64_t)(1 << 22)) big = true;
                     }
                 }
             }
         }
     }
     if (__syncthreads_or(wide)) return false;
+    const bool magic = !__syncthreads_or(big);
 
     {
         const int rr = threadIdx.x >> 4, l = threadIdx.x & 15;
@@ -434,13 +468,23 @@ __device__ __forceinline__ bool boxcar_tile(const BoxcarArgs &a, int tx, int ty,
             const PT *Q = Qs + (size_t)rr * nq;
             // points l + 16 j: two passes of eight over p < 256, then the
             // last two points (256, 257) on threads l = 0, 1
-            score_points<PT, kBxPass>(Q, d, s0, a.n_out, fit_end, l, interior, tile_block, a.wl, a.norm_block,
-                                      a.nblk, a.m0s, a.coefs, srow, krow);
-            score_points<PT, kBxPass>(Q, d, s0, a.n_out, fit_end, l + 16 * kBxPass, interior, tile_block, a.wl,
-                                      a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
-            if (l < kBxPts - 32 * kBxPass)
-                score_points<PT, 1>(Q, d, s0, a.n_out, fit_end, l + 32 * kBxPass, interior, tile_block, a.wl,
-                                    a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
+            if (sizeof(PT) == 4 && magic) {
+                score_points<PT, kBxPass, true>(Q, d, s0, a.n_out, fit_end, l, interior, tile_block, a.wl,
+                                                a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
+                score_points<PT, kBxPass, true>(Q, d, s0, a.n_out, fit_end, l + 16 * kBxPass, interior, tile_block,
+                                                a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
+                if (l < kBxPts - 32 * kBxPass)
+                    score_points<PT, 1, true>(Q, d, s0, a.n_out, fit_end, l + 32 * kBxPass, interior, tile_block,
+                                              a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
+            } else {
+                score_points<PT, kBxPass, false>(Q, d, s0, a.n_out, fit_end, l, interior, tile_block, a.wl,
+                                                 a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
+                score_points<PT, kBxPass, false>(Q, d, s0, a.n_out, fit_end, l + 16 * kBxPass, interior, tile_block,
+                                                 a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
+                if (l < kBxPts - 32 * kBxPass)
+                    score_points<PT, 1, false>(Q, d, s0, a.n_out, fit_end, l + 32 * kBxPass, interior, tile_block,
+                                               a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
+            }
         }
     }
     __syncthreads();

@@ -87,3 +87,8 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+    # a step is the sampled work: its time is what ran, the extrapolation is stated
+    assert line["extrapolated"] is True and 0 < line["trial_fraction"] < 1
+    assert abs(line["full_beam_s_extrapolated"] * line["trial_fraction"] - line["ms_per_step"] / 1e3) < 1e-6
+    beam_s = 16384 * 1.31072e-3
+    assert abs(line["value"] - beam_s * line["trial_fraction"] / (line["ms_per_step"] / 1e3)) < 1e-9 * line["value"]

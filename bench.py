@@ -221,6 +221,32 @@ def profiled_traffic(n_out: int):
     return float(prof["dram_bytes_per_launch_full_config"])
 
 
+def profiled_instructions_per_add():
+    """Lane instructions the dedispersion kernel issues per channel x DM x
+    sample add (smsp__inst_executed x 32 / adds of one ncu capture, committed
+    with the traffic summary), or None when the kernel source changed since."""
+    try:
+        prof = json.load(open(PROFILE_JSON))
+    except (OSError, ValueError):
+        return None
+    if prof.get("kernel_source_sha256_16") != kernel_source_hash() or "lane_instructions_per_add" not in prof:
+        return None
+    return float(prof["lane_instructions_per_add"])
+
+
+def issue_roofline(adds_tps: float, nsm: int):
+    """The dedispersion kernel against the SMs' instruction-issue rate (four
+    schedulers x 32 lanes per SM per clock at the maximum SM clock): lane
+    instructions per add (from the committed ncu capture) x adds per second."""
+    ipa = profiled_instructions_per_add()
+    if ipa is None:
+        return None
+    peak = nsm * 128 * MAX_SM_MHZ * 1e6 / 1e12
+    return {"lane_instructions_per_add": ipa, "achieved": adds_tps * ipa, "peak": peak,
+            "unit": "T lane-instructions/s", "frac": adds_tps * ipa / peak,
+            "peak_basis": f"{nsm} SMs x 4 schedulers x 32 lanes x {MAX_SM_MHZ:.0f} MHz"}
+
+
 def cpu_oracle_sample(wl, plan_delays, x, stride: int):
     """Time the oracle on every `stride`-th trial DM (full length, all
     channels): dedispersion + best-width S/N.  Returns (seconds for the full
@@ -379,6 +405,7 @@ def run_ours(args):
                      "kernel": "dedisperse_kernel",
                      "kernel_shape": dict(zip(("dm_tile", "time_tile", "chan_chunk"), sp.shape_info(plan.shape)))
                      | {"shape": plan.shape, "dm_tiles": plan.ntiles},
+                     "issue": issue_roofline(achieved, nsm),
                      "peak_basis": f"{nsm} SMs x {lanes:.1f} measured 32-bit add lanes/SM/clk x "
                                    f"{MAX_SM_MHZ:.0f} MHz"},
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
@@ -633,6 +660,9 @@ def stream_recall(plan, clf, freqs, widths, gulp: int, cap: int, kept_cap: int, 
     nchan, D = plan.nchan, plan.max_delay
     rounds = D // gulp
     per_dm = float(synth.fractional_delay(freqs, 1.0)[-1])
+    # RFI makes 10^4-10^5 candidates per gulp: a capacity that holds all of
+    # them, so that the sifter sees every candidate of every window
+    cap = 1 << 20
     s = sp.Stream(plan, nbeams, gulp, widths, 6.0, 8192, cap, 24 * (1 << 30) + nbeams * (gulp + D) * nchan,
                   max_batch=16)
     s.attach(clf, t_in=t_in, kept_cap=kept_cap)
@@ -659,9 +689,11 @@ def stream_recall(plan, clf, freqs, widths, gulp: int, cap: int, kept_cap: int, 
             s.push(b, noise[(b + k) % len(noise)])
     res = s.drain(with_cands=False, sifted=True)
     s.close()
-    kept_b = acc_b = injected = fp_sifter = fp_clf = overflow = 0
+    kept_b = acc_b = injected = fp_sifter = fp_clf = overflow = cand_overflow = n_cands = 0
     for info, _, kept, prob in res:
         k = int(info.seq)
+        n_cands += int(info.count)
+        cand_overflow += int(info.count) > cap
         win = [learning.Truth(bb.t0 - k * gulp, bb.dm, bb.fwhm, bb.snr) for bb in truths[int(info.beam)]
                if k * gulp <= bb.t0 < (k + 1) * gulp]
         which = learning.match_peaks(kept, plan.dms, widths, win)
@@ -678,7 +710,7 @@ def stream_recall(plan, clf, freqs, widths, gulp: int, cap: int, kept_cap: int, 
             "bursts_accepted": acc_b, "recall_vs_sifter": acc_b / max(kept_b, 1),
             "recall_vs_injected": acc_b / max(injected, 1), "snr_range": [8.0, 30.0],
             "non_burst_peaks_sifter": fp_sifter, "non_burst_peaks_accepted": fp_clf,
-            "gulps_over_kept_cap": overflow}
+            "candidates": n_cands, "gulps_over_candidate_cap": cand_overflow, "gulps_over_kept_cap": overflow}
 
 
 def run_stream(args):

@@ -275,6 +275,24 @@ int sp_single_pulse_search(const int32_t *d_dmt, int32_t ndm, int64_t n_out,
                            int64_t norm_block, void *d_work, int64_t work_bytes,
                            sp_cand *d_cands, int64_t cap, int64_t *d_count,
                            void *stream);
+/* sp_single_pulse_search with a (2 peak_radius + 1)^2 peak-filter window
+ * instead of 3 x 3 (Sec. 3.1.2: a window slides over the DM-time plane and
+ * keeps only its highest S/N; the paper uses 3 x 3 and 11 x 11 stencils,
+ * peak_radius 1 and 5).  A point at or above the threshold is kept when its
+ * best S/N is above every in-range neighbour of the window that precedes it
+ * in (dm_idx, t) order and not below any that follows.  peak_radius in
+ * 1..5; 1 is exactly sp_single_pulse_search.  For peak_radius > 1 the best-S/N
+ * map is written into the workspace first (ndm * n_out * 5 more bytes), so
+ * the workspace must hold sp_sps_window_workspace_bytes(...) bytes.
+ * Same arguments, outputs and errors otherwise (SP_EINVAL for a radius out of
+ * range). */
+int64_t sp_sps_window_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block,
+                                      int32_t peak_radius);
+int sp_single_pulse_search_window(const int32_t *d_dmt, int32_t ndm, int64_t n_out,
+                                  const int32_t *h_widths, int32_t nw, float threshold,
+                                  int64_t norm_block, int32_t peak_radius, void *d_work,
+                                  int64_t work_bytes, sp_cand *d_cands, int64_t cap,
+                                  int64_t *d_count, void *stream);
 /* Allocation-free variant of sp_single_pulse_search.  The paper has no
  * counterpart: this exists for callers that cannot allocate device memory
  * when they search -- a real-time loop that claimed its whole memory budget

@@ -12,6 +12,7 @@ shares no code with the CUDA library (``paper_2606_27262_gb300``): the C file
 * ``boxcar_snr``    Sec. 3.1.2, boxcar matched filter via the cumulative sum.
 * ``best``          Sec. 3.1.2, best S/N over the trial widths.
 * ``peaks``         Sec. 3.1.2, 3x3 peak filter in the DM-time plane + threshold.
+* ``peaks_window``  Sec. 3.1.2, the same with a (2r+1) x (2r+1) window (11 x 11: r = 5).
 * ``sift.sift``     Sec. 3.2.1, DBSCAN clustering, cluster peaks, thresholds (numpy).
 
 The shared library is compiled from ``oracle.c`` with gcc on first use
@@ -78,6 +79,8 @@ def _bind(lib):
     lib.oracle_best.restype = ctypes.c_int
     lib.oracle_peaks.argtypes = [P, P, i32, i64, f64, i32, i32, i32, P, i64]
     lib.oracle_peaks.restype = i64
+    lib.oracle_peaks_window.argtypes = [P, P, i32, i64, f64, i32, P, i64]
+    lib.oracle_peaks_window.restype = i64
     return lib
 
 
@@ -191,6 +194,20 @@ def peaks(best_map: np.ndarray, wbest: np.ndarray, thr: float, row0: int = 0,
     out = np.zeros(int(cap), dtype=CAND_DTYPE)
     n = lib.oracle_peaks(_p(b), _p(k), b.shape[0], b.shape[1], float(thr), int(row0),
                          int(emit_lo), int(emit_hi), _p(out), int(cap))
+    return out[: min(n, cap)].copy(), int(n)
+
+
+def peaks_window(best_map: np.ndarray, wbest: np.ndarray, thr: float, radius: int, cap: int = 1 << 20,
+                 lib=None):
+    """Candidates of a (2 radius + 1)^2 peak filter over the whole map, in
+    (dm, t) order, and the total count (may exceed ``cap``)."""
+    lib = lib or load()
+    b = np.ascontiguousarray(best_map, dtype=np.float64)
+    k = np.ascontiguousarray(wbest, dtype=np.int32)
+    out = np.zeros(int(cap), dtype=CAND_DTYPE)
+    n = lib.oracle_peaks_window(_p(b), _p(k), b.shape[0], b.shape[1], float(thr), int(radius), _p(out), int(cap))
+    if n < 0:
+        raise ValueError("oracle_peaks_window: radius must be >= 1")
     return out[: min(n, cap)].copy(), int(n)
 
 

@@ -23,6 +23,8 @@
  *   oracle_best        -- Sec. 3.1.2: multiple trial widths, keep the best.
  *   oracle_peaks       -- Sec. 3.1.2 peak filtering with a 3x3 window in the
  *                         DM-time plane, threshold in units of sigma.
+ *   oracle_peaks_window -- the same filter with a (2r+1) x (2r+1) window; the
+ *                         paper's second stencil is 11 x 11 (r = 5).
  *
  * Readings where the paper is silent (all stated, none hidden):
  *   - channel 0 is the highest frequency (the band is flipped so that the
@@ -324,6 +326,58 @@ int64_t oracle_peaks(const double *best, const int32_t *wbest, int32_t nrows,
                 continue;
             if (count < cap) {
                 out[count].dm_idx = row0 + r;
+                out[count].t = (int32_t)t;
+                out[count].width_idx = wbest[(int64_t)r * n_out + t];
+                out[count].pad_ = 0;
+                out[count].snr = v;
+            }
+            ++count;
+        }
+    }
+    return count;
+}
+
+/* Peak filter with a (2*radius+1) x (2*radius+1) window in the DM-time plane
+ * (Sec. 3.1.2: a window slides over the candidates and only the highest S/N
+ * of each window survives; the paper's stencils are 3 x 3 and 11 x 11) plus
+ * the threshold, over a whole best-S/N map.  (r, t) is kept when best >= thr
+ * and, for every in-range neighbour (r', t') of the window, best(r, t) >
+ * best(r', t') if (r', t') comes before (r, t) in (row, t) order and >=
+ * otherwise.  Output in (row, t) order; returns the total count (which may
+ * exceed cap: only the first cap are written). */
+int64_t oracle_peaks_window(const double *best, const int32_t *wbest, int32_t nrows,
+                            int64_t n_out, double thr, int32_t radius,
+                            oracle_cand *out, int64_t cap)
+{
+    if (radius < 1)
+        return -1;
+    int64_t count = 0;
+    for (int32_t r = 0; r < nrows; ++r) {
+        for (int64_t t = 0; t < n_out; ++t) {
+            const double v = best[(int64_t)r * n_out + t];
+            if (!(v >= thr))
+                continue;
+            int keep = 1;
+            for (int32_t dr = -radius; dr <= radius && keep; ++dr) {
+                for (int64_t dt = -radius; dt <= radius; ++dt) {
+                    if (dr == 0 && dt == 0)
+                        continue;
+                    const int32_t rr = r + dr;
+                    const int64_t tt = t + dt;
+                    if (rr < 0 || rr >= nrows || tt < 0 || tt >= n_out)
+                        continue;
+                    const double u = best[(int64_t)rr * n_out + tt];
+                    const int before = (dr < 0) || (dr == 0 && dt < 0);
+                    if (before ? !(v > u) : !(v >= u)) {
+                        keep = 0;
+                        break;
+                    }
+                }
+            }
+            if (!keep)
+                continue;
+            if (count < cap) {
+                out[count].dm_idx = r;
                 out[count].t = (int32_t)t;
                 out[count].width_idx = wbest[(int64_t)r * n_out + t];
                 out[count].pad_ = 0;

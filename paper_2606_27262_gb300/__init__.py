@@ -76,6 +76,9 @@ SIGNATURES = {
     "sp_searcher_run_host": (ctypes.c_int, [P, P, P, I64, P, P]),
     "sp_searcher_submit_host": (ctypes.c_int, [P, P, P]),
     "sp_debug_staging_fault": (ctypes.c_int, [ctypes.c_int32, I64]),
+    "sp_sps_window_workspace_bytes": (I64, [I32, I64, I32, I64, I32]),
+    "sp_single_pulse_search_window": (ctypes.c_int, [P, I32, I64, P, I32, ctypes.c_float, I64, I32, P, I64, P, I64,
+                                                     P, P]),
     "sp_searcher_collect": (ctypes.c_int, [P, P, I64, P]),
     "sp_dedisp_shape_info": (ctypes.c_int, [I32, P, P, P]),
     "sp_plan_create_shaped": (ctypes.c_int, [P, I32, F64, P, I32, I32, P]),
@@ -303,6 +306,23 @@ def single_pulse_search(d_dmt, widths, threshold: float, norm_block: int, d_work
                                          w.size, float(threshold), int(norm_block), _ptr(d_work),
                                          int(d_work.numel()), _ptr(d_cands), int(d_cands.shape[0]),
                                          _ptr(d_count), _stream(stream)), "sp_single_pulse_search")
+
+
+def sps_window_workspace_bytes(ndm: int, n_out: int, nw: int, norm_block: int, peak_radius: int) -> int:
+    return int(_lib().sp_sps_window_workspace_bytes(int(ndm), int(n_out), int(nw), int(norm_block),
+                                                    int(peak_radius)))
+
+
+def single_pulse_search_window(d_dmt, widths, threshold: float, norm_block: int, peak_radius: int, d_work, d_cands,
+                               d_count, stream=None):
+    """single_pulse_search with a (2 peak_radius + 1)^2 peak filter
+    (sp_single_pulse_search_window; 5 = the paper's 11 x 11 stencil)."""
+    w = _widths(widths)
+    _check(_lib().sp_single_pulse_search_window(_ptr(d_dmt), int(d_dmt.shape[0]), int(d_dmt.shape[1]), w.ctypes.data,
+                                                w.size, float(threshold), int(norm_block), int(peak_radius),
+                                                _ptr(d_work), int(d_work.numel()), _ptr(d_cands),
+                                                int(d_cands.shape[0]), _ptr(d_count), _stream(stream)),
+           "sp_single_pulse_search_window")
 
 
 SP_NOALLOC_SCRATCH_BYTES = 16 << 20

@@ -177,6 +177,30 @@ extern "C" int sp_single_pulse_search(const int32_t *d_dmt, int32_t ndm, int64_t
     return launch_sps(a, reinterpret_cast<cudaStream_t>(stream));
 }
 
+extern "C" int64_t sp_sps_window_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block,
+                                                 int32_t peak_radius) {
+    if (ndm <= 0 || n_out <= 0 || nw <= 0 || peak_radius < 1 || peak_radius > kMaxPeakRadius) return -1;
+    return sps_window_workspace_bytes(ndm, n_out, nw, norm_block, peak_radius);
+}
+
+extern "C" int sp_single_pulse_search_window(const int32_t *d_dmt, int32_t ndm, int64_t n_out,
+                                             const int32_t *h_widths, int32_t nw, float threshold,
+                                             int64_t norm_block, int32_t peak_radius, void *d_work,
+                                             int64_t work_bytes, sp_cand *d_cands, int64_t cap, int64_t *d_count,
+                                             void *stream) {
+    if (peak_radius < 1 || peak_radius > kMaxPeakRadius) return SP_EINVAL;
+    SpsArgs a;
+    int rc = sps_common(d_dmt, ndm, n_out, h_widths, nw, norm_block, d_work, work_bytes, a);
+    if (rc) return rc;
+    if (work_bytes < sps_window_workspace_bytes(ndm, n_out, nw, norm_block, peak_radius)) return SP_EWORKSPACE;
+    if (!d_count || cap < 0 || (cap > 0 && !d_cands)) return SP_EINVAL;
+    a.threshold = threshold;
+    a.cands = d_cands;
+    a.cap = cap;
+    a.count = d_count;
+    return launch_sps_window(a, peak_radius, reinterpret_cast<cudaStream_t>(stream));
+}
+
 extern "C" int sp_best_snr_map(const int32_t *d_dmt, int32_t ndm, int64_t n_out, const int32_t *h_widths,
                                int32_t nw, int64_t norm_block, void *d_work, int64_t work_bytes, float *d_best,
                                int8_t *d_wbest, void *stream) {

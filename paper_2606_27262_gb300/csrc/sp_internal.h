@@ -160,6 +160,10 @@ struct SpsArgs {
 int64_t sps_nblocks(int64_t n_out, int64_t norm_block);
 int64_t sps_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block);
 int launch_sps(const SpsArgs &a, cudaStream_t stream);
+// Windowed peak filter of radius 1..kMaxPeakRadius (radius 1 = launch_sps).
+constexpr int kMaxPeakRadius = 5;
+int64_t sps_window_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block, int32_t radius);
+int launch_sps_window(SpsArgs a, int32_t radius, cudaStream_t stream);
 // Sets the boxcar kernels' shared-memory limit for widths up to maxw on the
 // current device (launch_sps does it on first use otherwise).
 int sps_configure(int32_t maxw);

@@ -560,6 +560,77 @@ __global__ void __launch_bounds__(256, 1) sps_boxcar_wide_kernel(BoxcarArgs a) {
     }
 }
 
+// Peak filter with a (2R+1) x (2R+1) window (Sec. 3.1.2: the paper's
+// second stencil is 11 x 11, R = 5) over a best-S/N map the boxcar kernel
+// wrote: one CTA per 32 rows x 256 samples, staged with an R-wide halo (-inf
+// outside the map); a point at or above the threshold is kept when it is
+// above every neighbour that precedes it in (row, t) order and not below any
+// that follows (the same tie rule as the 3 x 3 filter); kept points are
+// appended with one atomic per warp.
+constexpr int kPkRows = 32;
+constexpr int kPkT = 256;
+
+__host__ __device__ inline size_t peaks_smem(int radius) {
+    return (size_t)(kPkRows + 2 * radius) * (kPkT + 2 * radius) * sizeof(float);
+}
+
+__global__ void __launch_bounds__(256) sps_peaks_window_kernel(const float *__restrict__ best,
+                                                               const int8_t *__restrict__ wbest, int32_t ndm,
+                                                               int64_t n_out, int radius, float thr,
+                                                               sp_cand *__restrict__ cands, int64_t cap,
+                                                               unsigned long long *__restrict__ count) {
+    extern __shared__ __align__(16) float tile[];
+    const int W = kPkT + 2 * radius;
+    const int H = kPkRows + 2 * radius;
+    const int64_t t0 = (int64_t)blockIdx.x * kPkT;
+    const int d0 = blockIdx.y * kPkRows;
+    for (int i = threadIdx.x; i < H * W; i += blockDim.x) {
+        const int rr = i / W, cc = i - rr * W;
+        const int d = d0 - radius + rr;
+        const int64_t t = t0 - radius + cc;
+        tile[i] = (d >= 0 && d < ndm && t >= 0 && t < n_out) ? __ldg(best + (int64_t)d * n_out + t) : -INFINITY;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kPkRows * kPkT; i += blockDim.x) {
+        const int r = i / kPkT, c = i - r * kPkT;
+        const int d = d0 + r;
+        const int64_t t = t0 + c;
+        const float v = tile[(r + radius) * W + c + radius];
+        bool keep = d < ndm && t < n_out && v >= thr;
+        for (int dr = -radius; dr <= radius && keep; ++dr) {
+            const float *row = tile + (r + radius + dr) * W + c + radius;
+            for (int dc = -radius; dc <= radius; ++dc) {
+                if (dr == 0 && dc == 0) continue;
+                const float u = row[dc];
+                const bool before = dr < 0 || (dr == 0 && dc < 0);
+                if (before ? !(v > u) : !(v >= u)) {
+                    keep = false;
+                    break;
+                }
+            }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, keep);
+        if (mask) {
+            const int leader = __ffs(mask) - 1;
+            unsigned long long basec = 0;
+            if (lane == leader) basec = atomicAdd(count, (unsigned long long)__popc(mask));
+            basec = __shfl_sync(0xffffffffu, basec, leader);
+            if (keep) {
+                const unsigned long long pos = basec + __popc(mask & ((1u << lane) - 1u));
+                if ((int64_t)pos < cap) {
+                    sp_cand cd;
+                    cd.dm_idx = d;
+                    cd.t = (int32_t)t;
+                    cd.width_idx = __ldg(wbest + (int64_t)d * n_out + t);
+                    cd.snr = v;
+                    cands[pos] = cd;
+                }
+            }
+        }
+    }
+}
+
 size_t boxcar_smem(int maxw) { return boxcar_smem_t<uint32_t>(maxw); }
 size_t boxcar_wide_smem(int maxw) { return boxcar_smem_t<int64_t>(maxw); }
 
@@ -677,6 +748,57 @@ int launch_sps(const SpsArgs &a, cudaStream_t stream) {
         sps_boxcar_wide_kernel<false><<<nsm, 256, boxcar_wide_smem(maxw), stream>>>(b);
     }
     note_launch(2);
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int64_t sps_window_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block, int32_t radius) {
+    const int64_t base = sps_workspace_bytes(ndm, n_out, nw, norm_block);
+    if (radius <= 1) return base;
+    return base + align256((int64_t)ndm * n_out * 4) + align256((int64_t)ndm * n_out);
+}
+
+// Radius 1: the fused 3 x 3 search.  Radius 2..kMaxPeakRadius: the best-S/N
+// map into the workspace's tail, then the windowed peak filter.
+int launch_sps_window(SpsArgs a, int32_t radius, cudaStream_t stream) {
+    if (radius <= 1) return launch_sps(a, stream);
+    uint8_t *tail = reinterpret_cast<uint8_t *>(a.work) + sps_workspace_bytes(a.ndm, a.n_out, a.nw, a.norm_block);
+    float *map = reinterpret_cast<float *>(tail);
+    int8_t *wmap = reinterpret_cast<int8_t *>(tail + align256((int64_t)a.ndm * a.n_out * 4));
+    sp_cand *cands = a.cands;
+    const int64_t cap = a.cap;
+    int64_t *count = a.count;
+    const float thr = a.threshold;
+    a.cands = nullptr;
+    a.count = nullptr;
+    a.cap = 0;
+    a.map_best = map;
+    a.map_wbest = wmap;
+    int rc = launch_sps(a, stream);
+    if (rc) return rc;
+    static std::mutex lock;
+    static size_t configured[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return SP_ECUDA;
+    }
+    const size_t smem = peaks_smem(radius);
+    {
+        std::lock_guard<std::mutex> guard(lock);
+        if (configured[dev] < smem) {
+            if (cudaFuncSetAttribute(sps_peaks_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess) {
+                cudaGetLastError();
+                return SP_ECUDA;
+            }
+            configured[dev] = smem;
+        }
+    }
+    if (cudaMemsetAsync(count, 0, sizeof(int64_t), stream) != cudaSuccess) return SP_ECUDA;
+    const dim3 grid((unsigned)((a.n_out + kPkT - 1) / kPkT), (unsigned)((a.ndm + kPkRows - 1) / kPkRows));
+    sps_peaks_window_kernel<<<grid, 256, smem, stream>>>(map, wmap, a.ndm, a.n_out, radius, thr, cands, cap,
+                                                         reinterpret_cast<unsigned long long *>(count));
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

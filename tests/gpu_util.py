@@ -69,9 +69,10 @@ def check_best_map(gb, gk, ob, ok, osnr=None):
         assert same.all(), f"{(~same).sum()} width indices differ"
 
 
-def check_candidates(g, o, ob, thr: float):
+def check_candidates(g, o, ob, thr: float, radius: int = 1):
     """Candidate sets equal except where a decision sits within SNR_RTOL of
-    a threshold or of a neighbour's value (G8: near-ties are don't-care)."""
+    a threshold or of a neighbour's value in the (2 radius + 1)^2 peak
+    window (G8: near-ties are don't-care)."""
     gs = {(int(a), int(b)) for a, b in zip(g["dm_idx"], g["t"])}
     os_ = {(int(a), int(b)) for a, b in zip(o["dm_idx"], o["t"])}
     ndm, n_out = ob.shape
@@ -80,8 +81,8 @@ def check_candidates(g, o, ob, thr: float):
         v = ob[d, t]
         if abs(v - thr) <= SNR_RTOL * max(abs(thr), 1):
             return True
-        for dd in (-1, 0, 1):
-            for dt in (-1, 0, 1):
+        for dd in range(-radius, radius + 1):
+            for dt in range(-radius, radius + 1):
                 e, u = d + dd, t + dt
                 if (dd or dt) and 0 <= e < ndm and 0 <= u < n_out and math.isfinite(ob[e, u]):
                     if abs(ob[e, u] - v) <= SNR_RTOL * max(abs(v), 1):

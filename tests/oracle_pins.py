@@ -302,6 +302,52 @@ def pin_best_and_peaks_bruteforce(lib):
     assert got == _py_peaks(m, 1.0) == [(0, 4), (1, 1), (2, 7)], got
 
 
+def _py_window_peaks(best, thr, radius):
+    """Brute force of the sliding-window rule: a point survives its
+    (2r+1)^2 window when it is at least the threshold, strictly above every
+    in-range point of the window that comes before it in (row, t) order and
+    not below any that comes after."""
+    nd, n = best.shape
+    out = []
+    for d in range(nd):
+        for t in range(n):
+            v = best[d, t]
+            if not v >= thr:
+                continue
+            window = [(e, u) for e in range(max(0, d - radius), min(nd, d + radius + 1))
+                      for u in range(max(0, t - radius), min(n, t + radius + 1)) if (e, u) != (d, t)]
+            if all((v > best[e, u]) if (e, u) < (d, t) else (v >= best[e, u]) for e, u in window):
+                out.append((d, t))
+    return out
+
+
+def pin_peaks_window_bruteforce(lib):
+    """The (2r+1)^2 peak filter (Sec. 3.1.2's 3x3 and 11x11 stencils):
+    equal to the brute force on random maps with many exact ties for r = 2
+    and 5, equal to the 3x3 filter for r = 1, and on a hand-made row an
+    11x11 window keeps only the higher of two peaks 4 samples apart while
+    3x3 keeps both."""
+    rng = np.random.default_rng(17)
+    for radius in (1, 2, 5):
+        b = np.round(rng.normal(0, 1.5, size=(14, 45)) * 2) / 2  # half-unit grid: many ties
+        b[rng.random(b.shape) < 0.05] = -np.inf
+        kk = np.zeros(b.shape, np.int32)
+        c, n = oracle.peaks_window(b, kk, 0.5, radius, lib=lib)
+        want = _py_window_peaks(b, 0.5, radius)
+        assert n == len(want) and [(int(a), int(t)) for a, t in zip(c["dm_idx"], c["t"])] == want, radius
+        if radius == 1:
+            c3, n3 = oracle.peaks(b, kk, 0.5, lib=lib)
+            assert [(int(a), int(t)) for a, t in zip(c3["dm_idx"], c3["t"])] == want
+    m = np.zeros((3, 16))
+    m[1, 4], m[1, 8] = 5.0, 6.0
+    kk = np.zeros(m.shape, np.int32)
+    got3 = [(int(a), int(t)) for a, t in zip(*(lambda c: (c["dm_idx"], c["t"]))(oracle.peaks_window(m, kk, 1.0, 1,
+                                                                                                   lib=lib)[0]))]
+    got11 = [(int(a), int(t)) for a, t in zip(*(lambda c: (c["dm_idx"], c["t"]))(oracle.peaks_window(m, kk, 1.0, 5,
+                                                                                                    lib=lib)[0]))]
+    assert got3 == [(1, 4), (1, 8)] and got11 == [(1, 8)], (got3, got11)
+
+
 # ------------------------------------------------------------ whole path --
 def pin_burst_recovered(lib):
     """A strong Gaussian burst at an on-grid DM in config-1 noise is found at
@@ -326,5 +372,6 @@ ALL_PINS = [
     pin_delays_exact, pin_delays_structure, pin_dedisperse_bruteforce, pin_dm0_channel_sum,
     pin_smearing_appendix_a, pin_snr_width1_standardisation, pin_snr_impulse_closed_form,
     pin_snr_blocks, pin_snr_large_values, pin_snr_zero_variance, pin_snr_white_noise, pin_best_and_peaks_bruteforce,
+    pin_peaks_window_bruteforce,
     pin_burst_recovered,
 ]

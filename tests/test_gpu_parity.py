@@ -167,6 +167,35 @@ def test_candidates_parity(ndm, n_out, widths, L, kind):
         gu.check_candidates(g, o, ob, thr)
 
 
+@pytest.mark.parametrize("radius", [2, 5])
+@pytest.mark.parametrize("ndm,n_out,widths,L,kind", [SPS_CASES[1], SPS_CASES[2], SPS_CASES[6]])
+def test_window_peaks_parity(ndm, n_out, widths, L, kind, radius):
+    """The (2r+1)^2 peak filter (the paper's 11 x 11 stencil is r = 5)
+    against the oracle's, and r = 1 equal to the fused 3 x 3 search."""
+    rng = np.random.default_rng(ndm + n_out + 3)
+    dmt = torch.from_numpy(_dmt_values(kind, ndm, n_out, rng)).cuda()
+    ob, ok = oracle.best(dmt.cpu().numpy(), widths, L)
+    for thr in (3.0, 0.0):
+        work = torch.empty(sp.sps_window_workspace_bytes(ndm, n_out, len(widths), L, radius), dtype=torch.uint8,
+                           device="cuda")
+        cands = torch.zeros((1 << 20, 4), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        sp.single_pulse_search_window(dmt, widths, thr, L, radius, work, cands, cnt)
+        torch.cuda.synchronize()
+        n = int(cnt.item())
+        g = sp.cands_to_numpy(cands.cpu().numpy(), n)
+        o, on = oracle.peaks_window(ob, ok, thr, radius)
+        assert n == g.size
+        gu.check_candidates(g, o, ob, thr, radius=radius)
+        g3, _ = gu.dev_candidates(dmt, widths, thr, L)
+        assert g.size <= g3.size  # a wider window keeps a subset of the 3 x 3 peaks (up to near-ties)
+        w1 = torch.empty(sp.sps_window_workspace_bytes(ndm, n_out, len(widths), L, 1), dtype=torch.uint8,
+                         device="cuda")
+        sp.single_pulse_search_window(dmt, widths, thr, L, 1, w1, cands, cnt)
+        torch.cuda.synchronize()
+        assert np.array_equal(sp.cands_to_numpy(cands.cpu().numpy(), int(cnt.item())), g3)
+
+
 def test_candidate_overflow():
     rng = np.random.default_rng(5)
     dmt = rng.integers(0, 1000, size=(40, 4000)).astype(np.int32)

@@ -34,6 +34,8 @@ MUTANTS = {
     "widest_on_ties": ("if (kb < 0 || v > b) {", "if (kb < 0 || v >= b) {"),
     "tie_rule_reversed": ("if (before ? !(v > u) : !(v >= u)) {", "if (before ? !(v >= u) : !(v > u)) {"),
     "threshold_strict": ("if (!(v >= thr))", "if (!(v > thr))"),
+    "window_radius_ignored": ("for (int32_t dr = -radius; dr <= radius && keep; ++dr) {",
+                              "for (int32_t dr = -1; dr <= 1 && keep; ++dr) {"),
     "no_dm_neighbours": ("for (int32_t dr = -1; dr <= 1 && keep; ++dr) {",
                          "for (int32_t dr = 0; dr <= 0 && keep; ++dr) {"),
 }

@@ -825,7 +825,8 @@ def run_stream(args):
 
     # Recall of the whole chain (search, sifter, classifier) on bursts
     # injected into the streamed beams themselves.
-    recall = stream_recall(plan, clf, freqs, widths, gulp, cap, kept_cap, t_in, dev, 2007 + 31 * rank,
+    # (every kept peak of a gulp scored: RFI leaves up to a few hundred)
+    recall = stream_recall(plan, clf, freqs, widths, gulp, cap, sp.SP_CNN_MAX_BATCH, t_in, dev, 2007 + 31 * rank,
                            args.stream_recall_beams)
 
     # Real-time arrivals near saturation: as many beams as 90 % of the

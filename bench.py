@@ -31,8 +31,8 @@ barriers and the slowest rank's time is reported.
 
 `--workload batched` measures the multi-beam step instead: 128 beams of
 4096 channels with lengths U{16384..131072} and max DM from {500, 1000,
-2000} (bandpass gains U(0.5, 1.5)), dedispersed in grouped persistent
-launches with the autotuned kernel shape and searched on a second stream,
+2000} (bandpass gains U(0.5, 1.5)), dedispersed in grouped launches (one
+CTA per work item) with the autotuned kernel shape and searched on a second stream,
 the whole step replayed as one CUDA graph; value = seconds of data searched
 per second, next to the same work as per-beam launches (also a graph).
 
@@ -107,7 +107,7 @@ def parse_args(argv=None):
     p.add_argument("--dmt-budget-gb", type=float, default=24.0,
                    help="batched workload: DM-transform bytes per group arena (GB)")
     p.add_argument("--no-per-beam", action="store_true", help="batched workload: skip the comparisons")
-    p.add_argument("--batch-mode", choices=["persistent", "grid"], default="persistent",
+    p.add_argument("--batch-mode", choices=["persistent", "grid"], default="grid",
                    help="batched workload: dedispersion launch style of the timed step (grid: one CTA per "
                         "work item; persistent: a resident grid draining a work queue)")
     return p.parse_args(argv)
@@ -467,7 +467,7 @@ def batched_e2e(args, batch, bw, data_s, stream, world, dev):
     return {"value": world * data_s / dt, "unit": "beams", "ms_per_step": dt * 1e3,
             "h2d_bytes_per_step": total,
             "d2h_bytes_per_step": int(8 * bw.nbeams + 16 * np.minimum(counts, cap_pb).sum()),
-            "api": "sp_batch_run_host (persistent grouped step; beams in page-locked host memory)"}
+            "api": "sp_batch_run_host (grouped step, one CTA per work item; beams in page-locked host memory)"}
 
 
 def run_batched(args):

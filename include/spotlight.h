@@ -418,7 +418,7 @@ int sp_searcher_collect(sp_searcher *s, sp_cand *h_cands, int64_t cap, int64_t *
  *   nchan bytes each; page-locked memory makes the copies asynchronous) into
  *   the beams' inputs group by group on a copy stream of the batch (group
  *   g + 1's copies overlap group g's work; each group waits only for its
- *   own), runs SP_BATCH_GROUPED, then copies every beam's count
+ *   own), runs SP_BATCH_GROUPED_GRID, then copies every beam's count
  *   to h_counts [nbeams] and its first min(count, cap_per_beam, cand_cap)
  *   candidates to h_cands + b * cap_per_beam.  Synchronises `stream`;
  *   SP_EOVERFLOW (after copying) if any beam overflowed.

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *ARCH, "-I", os.path.join(ROOT, "include")]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math"]
 
-CUDA_SOURCES = ["dedisperse.cu", "sps.cu", "sps_noalloc.cu", "probe.cu", "cnn.cu", "inject.cu"]
+CUDA_SOURCES = ["dedisperse.cu", "sps.cu", "sps_noalloc.cu", "probe.cu", "cnn.cu", "cnn_tc.cu", "inject.cu"]
 CXX_SOURCES = ["plan.cpp", "capi.cpp", "autotune.cpp", "batch.cpp", "stream.cpp", "sifter.cpp", "cnn.cpp"]
 
 
@@ -38,7 +38,7 @@ def cuda_home() -> str:
 
 def _sources():
     return [os.path.join(CSRC, s) for s in CUDA_SOURCES + CXX_SOURCES] + [
-        os.path.join(CSRC, "sp_internal.h"), os.path.join(ROOT, "include", "spotlight.h"),
+        os.path.join(CSRC, "sp_internal.h"), os.path.join(CSRC, "sp_cnn_internal.h"), os.path.join(ROOT, "include", "spotlight.h"),
         os.path.join(ROOT, "include", "spotlight_probe.h")]
 
 

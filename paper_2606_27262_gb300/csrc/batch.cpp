@@ -583,8 +583,8 @@ extern "C" int sp_batch_run_host(sp_batch *b, const uint8_t *const *h_in, sp_can
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     for (int32_t beam = 0; beam < b->nbeams; ++beam)
         if (!h_in[beam]) return SP_EINVAL;
-    int rc = run_grouped(b, st, false, true, h_in);
-    b->last_mode = rc ? b->last_mode : SP_BATCH_GROUPED;
+    int rc = run_grouped(b, st, false, false, h_in);  // one CTA per work item
+    b->last_mode = rc ? b->last_mode : SP_BATCH_GROUPED_GRID;
     b->timed_valid = false;
     if (rc) return rc;
     if (cudaMemcpyAsync(h_counts, b->d_counts, (size_t)b->nbeams * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

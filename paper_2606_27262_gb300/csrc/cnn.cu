@@ -570,6 +570,9 @@ int grid_for(int64_t n, int threads = 256) {
 
 int cnn_gemm(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int M, int N,
              int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st) {
+    // the tensor cores (tcgen05) where the shapes suit them
+    const int rc = cnn_gemm_tc(epi, A, lda, B, ldb, M, N, K, Cf, Cb, ldc, bias, splits, st);
+    if (rc != SP_ELIMIT) return rc;
     if (K % kBK) return SP_EINVAL;
     if (splits < 1) splits = 1;
     int64_t ks = ((K / kBK + splits - 1) / splits) * kBK;

@@ -16,6 +16,13 @@ constexpr int kEpiBiasRelu = 0, kEpiStore = 1, kEpiAtomic = 2;
 // `splits` K ranges in parallel; Cf zeroed by the caller).
 int cnn_gemm(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int M, int N,
              int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st);
+// The same product on the tensor cores (tcgen05, TMEM accumulator, TMA
+// operands; cnn_tc.cu): any K (zero past K), N a multiple of 16, M >= 64,
+// 16-byte aligned rows; SP_ELIMIT when a shape does not suit it.
+int cnn_gemm_tc(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int M, int N,
+                int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st);
+// Device status of the tensor-core GEMMs (bit 0: a wait ran out).
+int cnn_gemm_tc_status(int *h_status, bool clear);
 int cnn_im2col(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho, int Wo, int Kp,
                __nv_bfloat16 *cols, cudaStream_t st);
 int cnn_col2im_relu(const float *dcols, const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho,

@@ -150,81 +150,108 @@ __host__ __device__ inline size_t boxcar_smem_t(int maxw) {
     return (size_t)kBxRows * boxcar_nq(maxw) * sizeof(PT) + (size_t)kBxRows * kBxPts * 4 + (size_t)kBxRows * kBxPts;
 }
 
-// Phase 1 for one row, by one warp: Q[i] = sum_{j <= i} v(s0 + j) for the
-// staged indices i < nq, values outside [0, n_out) read as 0; 16 values per
-// lane (four 16-byte loads when rows are 16-byte aligned), an in-register
-// scan, then a warp scan of the lane totals.  Also the min and max of the
-// values read.
-template <typename PT>
-__device__ __forceinline__ void prefix_row(const int32_t *__restrict__ row, int64_t s0, int64_t n_out, bool vec,
-                                           int nq, PT *Q, int32_t &vmin, int32_t &vmax) {
-    const int lane = threadIdx.x & 31;
-    PT carry = 0;
-    for (int base0 = 0; base0 < nq; base0 += 512) {
-        if (nq - base0 <= 16) {  // a last chunk of one lane's width: lane 0 alone, no warp scan
-            if (lane == 0) {
-                PT acc = carry;
-                for (int e = 0; e < nq - base0; ++e) {
-                    const int64_t t = s0 + base0 + e;
-                    int32_t x = 0;
-                    if (t >= 0 && t < n_out) {
-                        x = __ldg(row + t);
-                        vmin = min(vmin, x);
-                        vmax = max(vmax, x);
-                    }
-                    acc += (PT)x;
-                    Q[base0 + e] = acc;
-                }
-            }
-            break;
+// Phase 1 for the two rows of one warp: Q[i] = sum_{j <= i} v(s0 + j) for
+// the staged indices i < nq of each row, values outside [0, n_out) (and
+// rows that are absent: row == nullptr) read as 0; also the min and max of
+// each row's values.  Chunks of 512 entries: 16 values per lane (four
+// 16-byte loads when rows are 16-byte aligned), both rows' loads issued
+// before either is scanned, an in-register scan, then a warp scan of the
+// lane totals; a last chunk of at most 16 entries is scanned by the 16
+// lanes of a half-warp per row.
+__device__ __forceinline__ void load_run16(const int32_t *__restrict__ row, int64_t t, int64_t n_out, bool vec,
+                                           bool active, int32_t (&v)[16], int32_t &vmin, int32_t &vmax) {
+    if (row && active && vec && t >= 0 && t + 16 <= n_out) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int4 x = __ldg(reinterpret_cast<const int4 *>(row + t) + q);
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
         }
-        const int base = base0 + lane * 16;
-        int32_t v[16];
-        const int64_t t = s0 + base;
-        if (base < nq && vec && t >= 0 && t + 16 <= n_out) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int4 x = __ldg(reinterpret_cast<const int4 *>(row + t) + q);
-                v[4 * q] = x.x;
-                v[4 * q + 1] = x.y;
-                v[4 * q + 2] = x.z;
-                v[4 * q + 3] = x.w;
-            }
+        for (int e = 0; e < 16; ++e) {
+            vmin = min(vmin, v[e]);
+            vmax = max(vmax, v[e]);
+        }
+    } else {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
+        for (int e = 0; e < 16; ++e) {
+            v[e] = 0;
+            if (row && active && t + e >= 0 && t + e < n_out) {
+                v[e] = __ldg(row + t + e);
                 vmin = min(vmin, v[e]);
                 vmax = max(vmax, v[e]);
             }
-        } else {
+        }
+    }
+}
+
+template <typename PT>
+__device__ __forceinline__ void scan_run16(const int32_t (&v)[16], bool active, int base, PT *Q, PT &carry) {
+    const int lane = threadIdx.x & 31;
+    PT r[16];
+    PT acc = 0;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                v[e] = 0;
-                if (base < nq && t + e >= 0 && t + e < n_out) {
-                    v[e] = __ldg(row + t + e);
-                    vmin = min(vmin, v[e]);
-                    vmax = max(vmax, v[e]);
+    for (int e = 0; e < 16; ++e) {
+        acc += (PT)v[e];
+        r[e] = acc;
+    }
+    PT incl = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const PT u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    const PT off = carry + incl - acc;
+    if (active) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) Q[base + e] = off + r[e];
+    }
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+}
+
+template <typename PT>
+__device__ __forceinline__ void prefix_rows2(const int32_t *__restrict__ rowA, const int32_t *__restrict__ rowB,
+                                             int64_t s0, int64_t n_out, bool vec, int nq, PT *QA, PT *QB,
+                                             int32_t &minA, int32_t &maxA, int32_t &minB, int32_t &maxB) {
+    const int lane = threadIdx.x & 31;
+    PT carryA = 0, carryB = 0;
+    for (int base0 = 0; base0 < nq; base0 += 512) {
+        if (nq - base0 <= 16) {  // last short chunk: lanes 0-15 row A, 16-31 row B
+            const bool isA = lane < 16;
+            const int e = lane & 15;
+            const int32_t *row = isA ? rowA : rowB;
+            const int64_t t = s0 + base0 + e;
+            const bool in = row != nullptr && e < nq - base0;
+            int32_t x = 0;
+            if (in && t >= 0 && t < n_out) {
+                x = __ldg(row + t);
+                if (isA) {
+                    minA = min(minA, x);
+                    maxA = max(maxA, x);
+                } else {
+                    minB = min(minB, x);
+                    maxB = max(maxB, x);
                 }
             }
-        }
-        PT r[16];
-        PT acc = 0;
+            PT incl = (PT)x;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            acc += (PT)v[e];
-            r[e] = acc;
+            for (int o = 1; o < 16; o <<= 1) {
+                const PT u = __shfl_up_sync(0xffffffffu, incl, o, 16);
+                if (e >= o) incl += u;
+            }
+            if (in) (isA ? QA : QB)[base0 + e] = (isA ? carryA : carryB) + incl;
+            break;
         }
-        PT incl = acc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const PT u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        const PT off = carry + incl - acc;
-        if (base < nq) {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) Q[base + e] = off + r[e];
-        }
-        carry += __shfl_sync(0xffffffffu, incl, 31);
+        const int base = base0 + lane * 16;
+        const bool active = base < nq;
+        const int64_t t = s0 + base;
+        int32_t vA[16], vB[16];
+        load_run16(rowA, t, n_out, vec, active, vA, minA, maxA);
+        load_run16(rowB, t, n_out, vec, active, vB, minB, maxB);
+        if (rowA) scan_run16<PT>(vA, active, base, QA, carryA);
+        if (rowB) scan_run16<PT>(vB, active, base, QB, carryB);
     }
 }
 
@@ -428,19 +455,24 @@ __device__ __forceinline__ bool boxcar_tile(const BoxcarArgs &a, int tx, int ty,
     const int64_t tile_block = bs == be ? bs : -1;
 
     bool wide = false, big = sizeof(PT) != 4;
-    for (int rr = 2 * warp; rr < 2 * warp + 2; ++rr) {
-        const int d = d0 - 1 + rr;
-        if (d < 0 || d >= a.ndm) continue;
-        int32_t vmin = INT32_MAX, vmax = INT32_MIN;
-        prefix_row<PT>(a.dmt + (int64_t)d * a.n_out, s0, a.n_out, vec, nq, Qs + (size_t)rr * nq, vmin, vmax);
+    {
+        const int dA = d0 - 1 + 2 * warp, dB = dA + 1;
+        const bool okA = dA >= 0 && dA < a.ndm, okB = dB >= 0 && dB < a.ndm;
+        int32_t mn[2] = {INT32_MAX, INT32_MAX}, mx[2] = {INT32_MIN, INT32_MIN};
+        prefix_rows2<PT>(okA ? a.dmt + (int64_t)dA * a.n_out : nullptr, okB ? a.dmt + (int64_t)dB * a.n_out : nullptr,
+                         s0, a.n_out, vec, nq, Qs + (size_t)(2 * warp) * nq, Qs + (size_t)(2 * warp + 1) * nq, mn[0],
+                         mx[0], mn[1], mx[1]);
         if (sizeof(PT) == 4) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-                vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-            }
-            if (vmin <= vmax) {
-                if (ts <= te) {
+            for (int h = 0; h < 2; ++h) {
+                const int d = dA + h;
+                int32_t vmin = mn[h], vmax = mx[h];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+                    vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+                }
+                if ((h ? okB : okA) && vmin <= vmax && ts <= te) {
                     for (int64_t b = bs + lane; b <= be; b += 32) {
                         const int64_t m0 = __ldg(a.m0s + (int64_t)d * a.nblk + b);
                         const int64_t dev = max((int64_t)vmax - m0, m0 - (int64_t)vmin);
@@ -466,24 +498,36 @@ __device__ __forceinline__ bool boxcar_tile(const BoxcarArgs &a, int tx, int ty,
             }
         } else {
             const PT *Q = Qs + (size_t)rr * nq;
-            // points l + 16 j: two passes of eight over p < 256, then the
-            // last two points (256, 257) on threads l = 0, 1
+            // points l + 16 j: two passes of eight over p < 256
             if (sizeof(PT) == 4 && magic) {
                 score_points<PT, kBxPass, true>(Q, d, s0, a.n_out, fit_end, l, interior, tile_block, a.wl,
                                                 a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
                 score_points<PT, kBxPass, true>(Q, d, s0, a.n_out, fit_end, l + 16 * kBxPass, interior, tile_block,
                                                 a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
-                if (l < kBxPts - 32 * kBxPass)
-                    score_points<PT, 1, true>(Q, d, s0, a.n_out, fit_end, l + 32 * kBxPass, interior, tile_block,
-                                              a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
             } else {
                 score_points<PT, kBxPass, false>(Q, d, s0, a.n_out, fit_end, l, interior, tile_block, a.wl,
                                                  a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
                 score_points<PT, kBxPass, false>(Q, d, s0, a.n_out, fit_end, l + 16 * kBxPass, interior, tile_block,
                                                  a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
-                if (l < kBxPts - 32 * kBxPass)
-                    score_points<PT, 1, false>(Q, d, s0, a.n_out, fit_end, l + 32 * kBxPass, interior, tile_block,
-                                               a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, srow, krow);
+            }
+        }
+        // The last two points (256, 257) of all 16 rows: one warp, one point
+        // per lane, instead of two threads in each row's half-warp.
+        static_assert(kBxPts - 32 * kBxPass == 2 && kBxRows * 2 == 32, "one tail point per lane of one warp");
+        if (threadIdx.x < 32) {
+            const int tr = threadIdx.x >> 1, tp = 32 * kBxPass + (threadIdx.x & 1);
+            const int td = d0 - 1 + tr;
+            float *tsrow = snr_s + tr * kBxPts;
+            int8_t *tkrow = k_s + tr * kBxPts;
+            if (td < 0 || td >= a.ndm) {
+                tsrow[tp] = -INFINITY;
+                tkrow[tp] = -1;
+            } else if (sizeof(PT) == 4 && magic) {
+                score_points<PT, 1, true>(Qs + (size_t)tr * nq, td, s0, a.n_out, fit_end, tp, interior, tile_block,
+                                          a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, tsrow, tkrow);
+            } else {
+                score_points<PT, 1, false>(Qs + (size_t)tr * nq, td, s0, a.n_out, fit_end, tp, interior, tile_block,
+                                           a.wl, a.norm_block, a.nblk, a.m0s, a.coefs, tsrow, tkrow);
             }
         }
     }

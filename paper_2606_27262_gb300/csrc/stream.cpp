@@ -360,11 +360,12 @@ int launch_batch(sp_stream *s, int li) {
         B.d_item_begin = L.d_begin;
         B.d_counter = L.d_counter;
         B.d_status = L.d_status;
-        // A persistent grid holds every SM until the batch is done, so the
-        // classifier's kernels could not start before then; with a
-        // classifier attached each item gets its own CTA, and the
-        // high-priority classifier CTAs take SMs as items retire.
-        if (!rc) rc = launch_dedisperse_batch(B, st, s->clf == nullptr);
+        // One CTA per work item: CTAs retire, so the search's and the
+        // classifier's high-priority CTAs take SMs as items finish (a
+        // persistent grid would hold every SM until the batch is done), and
+        // with eight DMs per thread the per-item kernel is also the faster
+        // one (the persistent loop's extra state spills registers).
+        if (!rc) rc = launch_dedisperse_batch(B, st, false);
     }
     // The searches go to the high-priority search stream: the next batch's
     // dedispersion (already queued on the other launch stream) would

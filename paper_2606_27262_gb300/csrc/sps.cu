@@ -584,7 +584,7 @@ __device__ __forceinline__ bool boxcar_tile(const BoxcarArgs &a, int tx, int ty,
 // Fast pass: every tile in 32-bit prefix arithmetic; a tile that cannot
 // prove its window sums exact is listed for the 64-bit pass.
 template <bool MAP>
-__global__ void __launch_bounds__(256, 3) sps_boxcar_kernel(BoxcarArgs a) {
+__global__ void __launch_bounds__(256, 4) sps_boxcar_kernel(BoxcarArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     if (!boxcar_tile<uint32_t, MAP>(a, blockIdx.x, blockIdx.y, smem) && threadIdx.x == 0) {
         const int slot = atomicAdd(a.wide_count, 1);

@@ -260,7 +260,8 @@ int sp_dedisperse_batch(const sp_batch_beam *h_beams, int32_t nbeams, void *d_wo
  *   h_widths [nw]      host, strictly increasing, 1..SP_MAX_WIDTH,
  *                      nw <= SP_MAX_WIDTHS.
  *   d_work/work_bytes  device scratch of sp_sps_workspace_bytes(...) bytes,
- *                      256-byte aligned (per-row block statistics).
+ *                      256-byte aligned (per-row block statistics,
+ *                      pre-filter constants and tile lists).
  *   d_cands [cap]      device; receives min(count, cap) candidates in an
  *                      unspecified order (sort by (dm_idx, t) for a
  *                      canonical list).
@@ -304,7 +305,7 @@ int sp_single_pulse_search_window(const int32_t *d_dmt, int32_t ndm, int64_t n_o
  * SP_NOALLOC_SCRATCH_BYTES (16 MiB), present on every GPU that loads the
  * library until the process exits.  Requests whose statistics need more
  * (sp_sps_workspace_bytes(ndm, n_out, nw, norm_block) > 16 MiB; config 2,
- * 5751 DMs x 131072 samples / 8192-sample blocks x 9 widths, needs 8.7 MB)
+ * 5751 DMs x 131072 samples / 8192-sample blocks x 9 widths, needs 15.9 MB)
  * return SP_ELIMIT.  The call allocates nothing: no cudaMalloc, no cudaFree.
  * The first call on a device looks up the array's device address with that
  * device current (make that first call before any stream capture) and keeps

@@ -6,17 +6,31 @@
 // Kernels:
 //   sps_stats_kernel   one CTA per (row, normalisation block): exact sum
 //                      (64-bit) and sum of squares (128-bit: int32 values
-//                      near 2^31 square to 2^62 each), 16-byte loads, the
-//                      128-bit variance term, and per-width float
-//                      coefficients of the S/N affine map.
-//   sps_boxcar_kernel  one CTA per 14 rows x 256 samples (+1 halo row and
-//                      sample on each side).  Stages prefix sums of the rows
-//                      in shared memory (warp-shuffle scans), evaluates every
-//                      width for every (row, sample), keeps the best, then
-//                      applies the threshold and the 3x3 rule from the staged
-//                      best-S/N tile and appends candidates with one atomic
-//                      per warp.  A template switch writes the best-S/N map
-//                      instead of candidates.
+//                      near 2^31 square to 2^62 each), 16-byte loads.
+//   sps_coef_kernel    one thread per (row, block): m0, the 128-bit
+//                      variance term, the per-width float coefficients of the
+//                      S/N affine map and the candidate pre-filter constants.
+//   sps_stream_kernel  candidate search for power-of-two widths: one CTA per
+//                      14 rows (+1 halo row on each side) and a segment of
+//                      chunks of 256 samples, walked with a two-chunk ring of
+//                      prefix sums per row; an integer pre-filter per point
+//                      and width, the exact S/N where it passes, the
+//                      threshold and the 3x3 peak filter, one atomic per warp
+//                      for the candidate append.  Chunks it cannot prove
+//                      exact in 32-bit float-convertible arithmetic, and the
+//                      beam's last chunk(s), are listed for the tile kernel.
+//   sps_boxcar_kernel  the tile kernel: one CTA per 14 rows x 256 samples
+//                      (+1 halo row and sample on each side).  Stages prefix
+//                      sums of the rows in shared memory (warp-shuffle scans),
+//                      evaluates every width for every (row, sample), keeps
+//                      the best, then applies the threshold and the 3x3 rule
+//                      from the staged best-S/N tile.  A template switch
+//                      writes the best-S/N map instead of candidates.  Runs
+//                      as a grid (best-S/N map, width lists the streamed
+//                      kernel does not take) or over a tile list
+//                      (sps_boxcar_listed_kernel).
+//   sps_boxcar_wide_kernel  the tile kernel in 64-bit prefix arithmetic over
+//                      the tiles the 32-bit passes listed.
 //
 // S/N arithmetic.  For block b of row d with count n, sum Sx, sum of squares
 // Sxx, let m0 = floor(Sx/n) and f = Sx/n - m0.  For a window sum S of width w
@@ -65,10 +79,17 @@ __device__ __forceinline__ uint64_t sq2(int32_t a, int32_t b) {
     return (uint64_t)((int64_t)a * a) + (uint64_t)((int64_t)b * b);
 }
 
+// Block sums: one CTA per (row, block) streams the block once (16-byte
+// loads, four in flight per thread) and writes its count's sum Sx (int64)
+// and sum of squares Sxx (128-bit, as two 64-bit words).
+struct BlockSums {
+    int64_t s1;
+    uint64_t s2_lo, s2_hi;
+};
+
 __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restrict__ dmt, int64_t n_out,
-                                                        int64_t norm_block, int64_t nblk, WidthList wl,
-                                                        int32_t *__restrict__ m0_out,
-                                                        float2 *__restrict__ coef_out) {
+                                                        int64_t norm_block, int64_t nblk,
+                                                        BlockSums *__restrict__ sums) {
     __shared__ int64_t red1[8];
     __shared__ u128 red2[8];
     const int64_t b = blockIdx.x;
@@ -106,8 +127,6 @@ __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restric
         red2[threadIdx.x >> 5] = s2;
     }
     __syncthreads();
-    __shared__ double s_frac, s_inv_sigma;
-    const int64_t idx = d * nblk + b;
     if (threadIdx.x == 0) {
         int64_t S1 = 0;
         u128 S2 = 0;
@@ -115,21 +134,78 @@ __global__ void __launch_bounds__(256) sps_stats_kernel(const int32_t *__restric
             S1 += red1[i];
             S2 += red2[i];
         }
-        const int64_t n = hi - lo;
-        int64_t m0 = S1 / n;
-        if (S1 - m0 * n < 0) --m0;  // floor for negative sums
-        s_frac = (double)(S1 - m0 * n) / (double)n;
-        // n <= 2^31 and S2 <= n * 2^62: the product stays below 2^124.
-        const __int128 var_n2 = (__int128)n * (__int128)S2 - (__int128)S1 * S1;
-        s_inv_sigma = var_n2 > 0 ? (double)n / sqrt((double)var_n2) : 0.0;
-        m0_out[idx] = (int32_t)m0;
+        BlockSums o;
+        o.s1 = S1;
+        o.s2_lo = (uint64_t)S2;
+        o.s2_hi = (uint64_t)(S2 >> 64);
+        sums[d * nblk + b] = o;
     }
-    __syncthreads();
-    if ((int)threadIdx.x < wl.nw) {  // one width per thread
-        const int k = threadIdx.x;
+}
+
+// sqrt(w) and 1/sqrt(w) of each width, in double (computed on the host).
+struct WidthRoots {
+    double sw[SP_MAX_WIDTHS], rsw[SP_MAX_WIDTHS];
+};
+
+// Pre-filter bound of the streamed candidate search: an integer X such that
+// every window with x = S - w*m0 < X has an S/N below thr in the search's
+// float arithmetic (snr = fmaf((float)x, cx, -cy), one rounding), also after
+// the search clears the low four mantissa bits of a negative S/N (which
+// raises it by less than 2^-19 of its size): thr is lowered by 2^-15 of its
+// size (and 2^-100), multiplied by rcx, a reciprocal of cx to within 2^-23
+// relative (so the quotient is within 1/2 of (t + cy)/cx where that is below
+// 2^23 in magnitude), rounded down and lowered by two more.  Clamped to
+// [-2^30, 2^30]: -2^30 lets every window through, 2^30 none (the search's |x|
+// stays below 2^22, so an error in a bound beyond 2^23 decides nothing).
+__device__ int32_t prefilter_bound(float thr, float cx, float cy, double rcx) {
+    constexpr double kLim = 1073741824.0;
+    if (thr != thr) return (int32_t)kLim;                      // NaN: nothing reaches it
+    if (isinf(thr)) return thr > 0.0f ? (int32_t)kLim : -(int32_t)kLim;
+    if (!(cx > 0.0f)) return thr <= 0.0f ? -(int32_t)kLim : (int32_t)kLim;  // zero variance: snr = 0
+    const double t = (double)thr - fabs((double)thr) * 0x1p-15 - 0x1p-100;
+    const double x = floor((t + (double)cy) * rcx) - 2.0;
+    if (!(x > -kLim)) return -(int32_t)kLim;
+    if (x >= kLim) return (int32_t)kLim;
+    return (int32_t)x;
+}
+
+// Per (row, block), one thread each: m0 = floor(Sx/n), f = Sx/n - m0, the
+// per-width float coefficients of the S/N affine map (inv = n/(sqrt(w)
+// sqrt(V)), bias = w f inv) and the pre-filter constants w*m0 + X (32-bit
+// wrap-around: the search subtracts them from a window's prefix difference
+// to get x - X exactly).  The double arithmetic runs here, spread over
+// threads, not at the end of every reduction CTA.
+__global__ void __launch_bounds__(256) sps_coef_kernel(const BlockSums *__restrict__ sums, int64_t nrb,
+                                                       int64_t n_out, int64_t norm_block, int64_t nblk,
+                                                       WidthList wl, WidthRoots wr, float thr,
+                                                       int32_t *__restrict__ m0_out, float2 *__restrict__ coef_out,
+                                                       uint32_t *__restrict__ cthr_out) {
+    const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (idx >= nrb) return;
+    const int64_t b = idx % nblk;
+    const int64_t lo = (nblk == 1) ? 0 : b * norm_block;
+    const int64_t hi = (b == nblk - 1) ? n_out : (b + 1) * norm_block;
+    const int64_t n = hi - lo;
+    const BlockSums sm = sums[idx];
+    const int64_t S1 = sm.s1;
+    const u128 S2 = ((u128)sm.s2_hi << 64) | sm.s2_lo;
+    int64_t m0 = S1 / n;
+    if (S1 - m0 * n < 0) --m0;  // floor for negative sums
+    const double rn = 1.0 / (double)n;
+    const double frac = (double)(S1 - m0 * n) * rn;
+    // n <= 2^31 and S2 <= n * 2^62: the product stays below 2^124.
+    const __int128 var_n2 = (__int128)n * (__int128)S2 - (__int128)S1 * S1;
+    const double sq = var_n2 > 0 ? sqrt((double)var_n2) : 0.0;
+    const double inv_sigma = var_n2 > 0 ? (double)n / sq : 0.0;
+    const double sig_n = sq * rn;
+    m0_out[idx] = (int32_t)m0;
+    for (int k = 0; k < wl.nw; ++k) {
         const double w = (double)wl.w[k];
-        const double inv = s_inv_sigma / sqrt(w);
-        coef_out[idx * wl.nw + k] = make_float2((float)inv, (float)(w * s_frac * inv));
+        const double inv = inv_sigma * wr.rsw[k];
+        const float cx = (float)inv, cy = (float)(w * frac * inv);
+        coef_out[idx * wl.nw + k] = make_float2(cx, cy);
+        cthr_out[idx * wl.nw + k] =
+            (uint32_t)wl.w[k] * (uint32_t)m0 + (uint32_t)prefilter_bound(thr, cx, cy, wr.sw[k] * sig_n);
     }
 }
 
@@ -429,6 +505,13 @@ struct BoxcarArgs {
     int *wide_count;  // tiles the 32-bit pass could not prove exact
     int2 *wide_list;
     bool vec;         // rows 16-byte aligned: 16-byte loads
+    // Streamed search: chunks [0, n_fast) of every row group, pre-filter
+    // constants w*m0 + X per (row, block, width), and the tiles it leaves
+    // to the tile kernel.
+    int32_t n_fast;
+    const uint32_t *cthr;
+    int *slow_count;
+    int2 *slow_list;
 };
 
 // One tile (14 rows x 256 samples + halo).  PT = uint32: prefix sums in
@@ -592,6 +675,23 @@ __global__ void __launch_bounds__(256, 4) sps_boxcar_kernel(BoxcarArgs a) {
     }
 }
 
+// The tiles the streamed search listed (the beam's last chunk(s) of every
+// row group and the chunks it could not prove exact in 2^22), in the 32-bit
+// tile kernel (persistent grid); a tile it cannot prove exact goes on to the
+// 64-bit pass.
+__global__ void __launch_bounds__(256, 4) sps_boxcar_listed_kernel(BoxcarArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int n = *a.slow_count;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const int2 tile = a.slow_list[i];
+        if (!boxcar_tile<uint32_t, false>(a, tile.x, tile.y, smem) && threadIdx.x == 0) {
+            const int slot = atomicAdd(a.wide_count, 1);
+            a.wide_list[slot] = tile;
+        }
+        __syncthreads();
+    }
+}
+
 // Exact pass over the listed tiles, 64-bit prefix sums (persistent grid).
 template <bool MAP>
 __global__ void __launch_bounds__(256, 1) sps_boxcar_wide_kernel(BoxcarArgs a) {
@@ -601,6 +701,338 @@ __global__ void __launch_bounds__(256, 1) sps_boxcar_wide_kernel(BoxcarArgs a) {
         const int2 tile = a.wide_list[i];
         boxcar_tile<int64_t, MAP>(a, tile.x, tile.y, smem);
         __syncthreads();
+    }
+}
+
+// Streamed candidate search (3x3 peaks).  One CTA per 14 DM rows (+1 halo
+// row on each side) and a segment of kStSeg chunks of 256 samples, walked
+// chunk by chunk.  Per staged row the CTA keeps the exclusive prefix sums
+// R[t] = sum_{s < t} v(s) of two consecutive chunks in a ring of 512 entries
+// (R[t] at t mod 512; the sums start at the segment's first sample, which
+// cancels in every difference), so each sample is loaded and scanned once.
+// The window sum of point t and width w is R[t + w] - R[t].
+//
+// Pre-filter: with C_w = w*m0 + X_w (X_w from prefilter_bound, per row,
+// block and width), max_w (R[t + w] - R[t] - C_w) < 0 shows that no width of
+// point t reaches the threshold; its S/N is recorded as -inf, which leaves
+// every 3x3 decision as it was (a candidate is at or above the threshold, so
+// it is above a neighbour that is below it, whatever that neighbour's
+// value).  A point that passes gets the exact S/N of the tile kernel's
+// check-free path.  A chunk whose window sums are not proven below 2^22 in
+// magnitude (per row: w_max * max|v - m0| over the samples t0-1 .. t0+511,
+// against the blocks of t0-1, t0 and t0+256) is listed for the tile kernel.
+// Used when the widths are 1, 2, 4, ..., 2^(nw-1) <= 256, rows are 16-byte
+// aligned, blocks are a multiple of 256 samples (or one block), for the
+// chunks c < n_out/256 - 1 (chunk c+1 lies inside the beam).
+constexpr int kStRing = 512;
+constexpr int kStSS = 264;  // staged S/N row stride: sample t0+p at index 4+p, p in [-1, 256]
+constexpr int kStSeg = 16;  // chunks per CTA
+
+__host__ __device__ inline size_t stream_smem() {
+    return (size_t)kBxRows * kStRing * 4 + (size_t)kBxRows * kStSS * 4 + (size_t)kBxRows * kStSS;
+}
+
+__device__ __forceinline__ uint4 lds128(const uint32_t *p) { return *reinterpret_cast<const uint4 *>(p); }
+
+// Chunk k of one staged row, by the 16 threads of a half-warp: thread l
+// holds the samples 256k + 64m + 4l + e (m, e < 4), 16-byte loads that are
+// contiguous across the half-warp.  A row that is absent (row == nullptr)
+// reads as zeros.
+__device__ __forceinline__ void stream_load(const int32_t *__restrict__ row, int64_t k, int l, int4 (&q)[4]) {
+    if (row) {
+        const int4 *src = reinterpret_cast<const int4 *>(row + k * 256 + 4 * l);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) q[m] = __ldg(src + 16 * m);
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) q[m] = make_int4(0, 0, 0, 0);
+    }
+}
+
+// The exclusive prefix of the loaded chunk k into ring slot k & 1,
+// continuing `carry` (16-byte stores, contiguous across the half-warp), and
+// the chunk's min and max.
+__device__ __forceinline__ void stream_scan(const int4 (&q)[4], int64_t k, uint32_t *ring, int l, uint32_t &carry,
+                                            int32_t &vmin, int32_t &vmax) {
+    uint32_t g[4], incl[4];
+    int32_t mn = INT32_MAX, mx = INT32_MIN;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        g[m] = (uint32_t)q[m].x + (uint32_t)q[m].y + (uint32_t)q[m].z + (uint32_t)q[m].w;
+        incl[m] = g[m];
+        mn = min(min(mn, min(q[m].x, q[m].y)), min(q[m].z, q[m].w));
+        mx = max(max(mx, max(q[m].x, q[m].y)), max(q[m].z, q[m].w));
+    }
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl[m], o, 16);
+            if (l >= o) incl[m] += u;
+        }
+    }
+    uint32_t base = carry;
+    uint32_t *dst = ring + (int)(k & 1) * 256 + 4 * l;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl[m], 15, 16);
+        uint4 o;
+        o.x = base + incl[m] - g[m];
+        o.y = o.x + (uint32_t)q[m].x;
+        o.z = o.y + (uint32_t)q[m].y;
+        o.w = o.z + (uint32_t)q[m].z;
+        *reinterpret_cast<uint4 *>(dst + 64 * m) = o;
+        base += tot;
+    }
+    carry = base;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o, 16));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o, 16));
+    }
+    vmin = mn;
+    vmax = mx;
+}
+
+// Chunk c's magic-range proof for one staged row, by three lanes of the
+// row's half-warp (lane j checks the block of sample t0 - 1, t0 or t0 + 256):
+// false when some window sum S - w*m0 of the chunk's points (t0-1 .. t0+256)
+// may reach 2^22 in magnitude.  [vmin, vmax] covers the samples t0 .. t0+511;
+// a window is at most w_max * max|v - m0|, and lim = (2^22 - 1) / w_max.
+__device__ __forceinline__ bool stream_proof(const BoxcarArgs &a, const int32_t *__restrict__ row, int64_t d,
+                                             int64_t c, int j, int32_t vmin, int32_t vmax, int64_t lim) {
+    const int64_t t0 = c * 256;
+    if (j > 2 || (j == 0 && t0 == 0)) return true;
+    const int64_t t = j == 0 ? t0 - 1 : (j == 1 ? t0 : t0 + 256);
+    int64_t lo = vmin, hi = vmax;
+    if (t0 > 0) {
+        const int64_t v = __ldg(row + t0 - 1);
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+    const int64_t m0 = __ldg(a.m0s + d * a.nblk + block_of(t, a.norm_block, a.nblk));
+    return hi - m0 <= lim && m0 - lo <= lim;
+}
+
+// Exact S/N of one point over all widths (the tile kernel's check-free
+// formula): Rw(k) = R[t + 2^k], Rt = R[t].  Returns the S/N and sets kbest.
+template <typename RW>
+__device__ __forceinline__ float stream_exact(RW Rw, uint32_t Rt, int nw, int32_t m0, const float2 *__restrict__ cf,
+                                              int &kbest) {
+    float best = -INFINITY;
+    for (int k = 0; k < nw; ++k) {
+        const uint32_t w = 1u << k;
+        const uint32_t xs = Rw(k) - Rt + (kMagicBits - w * (uint32_t)m0);
+        const float2 c = __ldg(cf + k);
+        const float sv = fmaf(__uint_as_float(xs) - kMagicValue, c.x, -c.y);
+        best = fmaxf(best, __uint_as_float((__float_as_uint(sv) & ~15u) | (15u - (uint32_t)k)));
+    }
+    const uint32_t bits = __float_as_uint(best);
+    kbest = 15 - (int)(bits & 15u);
+    return __uint_as_float(bits & ~15u);
+}
+
+// Pre-filter of four consecutive points (ring index i0, 16-byte aligned):
+// a[e] = max_k (R[t_e + 2^k] - R[t_e] - C_k) as a 32-bit signed value.  NW
+// widths when NW > 0, else nw (at most 9).
+template <int NW>
+__device__ __forceinline__ void stream_prefilter4(const uint32_t *ring, int i0, int nw, const uint32_t (&cw)[9],
+                                                  uint4 &B, int32_t (&a)[4]) {
+    const int n = NW > 0 ? NW : nw;
+    B = lds128(ring + i0);
+    const uint4 N = lds128(ring + ((i0 + 4) & (kStRing - 1)));
+    a[0] = (int32_t)(B.y - B.x - cw[0]);
+    a[1] = (int32_t)(B.z - B.y - cw[0]);
+    a[2] = (int32_t)(B.w - B.z - cw[0]);
+    a[3] = (int32_t)(N.x - B.w - cw[0]);
+    if (n > 1) {
+        a[0] = max(a[0], (int32_t)(B.z - B.x - cw[1]));
+        a[1] = max(a[1], (int32_t)(B.w - B.y - cw[1]));
+        a[2] = max(a[2], (int32_t)(N.x - B.z - cw[1]));
+        a[3] = max(a[3], (int32_t)(N.y - B.w - cw[1]));
+    }
+    if (n > 2) {
+        a[0] = max(a[0], (int32_t)(N.x - B.x - cw[2]));
+        a[1] = max(a[1], (int32_t)(N.y - B.y - cw[2]));
+        a[2] = max(a[2], (int32_t)(N.z - B.z - cw[2]));
+        a[3] = max(a[3], (int32_t)(N.w - B.w - cw[2]));
+    }
+#pragma unroll
+    for (int k = 3; k < 9; ++k) {
+        if (k < n) {
+            const uint4 V = lds128(ring + ((i0 + (1 << k)) & (kStRing - 1)));
+            a[0] = max(a[0], (int32_t)(V.x - B.x - cw[k]));
+            a[1] = max(a[1], (int32_t)(V.y - B.y - cw[k]));
+            a[2] = max(a[2], (int32_t)(V.z - B.z - cw[k]));
+            a[3] = max(a[3], (int32_t)(V.w - B.w - cw[k]));
+        }
+    }
+}
+
+// Halo point of chunk c (t0 - 1 or t0 + 256) of staged row hr: its S/N, or
+// -inf where the pre-filter shows that no width reaches the threshold or the
+// point lies before the beam.
+__device__ __forceinline__ float stream_halo(const BoxcarArgs &a, const uint32_t *ring_all, int d0, int hr,
+                                             bool right, int64_t t0, int nw) {
+    const int64_t hd = (int64_t)d0 - 1 + hr;
+    const int64_t t = right ? t0 + 256 : t0 - 1;
+    if (t < 0) return -INFINITY;
+    const int t0m = (int)(t0 & (kStRing - 1));
+    const int32_t *hrow = a.dmt + hd * a.n_out;
+    const uint32_t *hring = ring_all + hr * kStRing;
+    const uint32_t Rt = right ? hring[(t0m + 256) & (kStRing - 1)] : hring[t0m] - (uint32_t)__ldg(hrow + t0 - 1);
+    // R[t0 + 512] = R[t0 + 511] + v(t0 + 511)
+    const uint32_t Rend = right ? hring[(t0m + 511) & (kStRing - 1)] + (uint32_t)__ldg(hrow + t0 + 511) : 0u;
+    auto Rw = [&](int k) -> uint32_t {
+        const int64_t j = t + (1 << k);
+        return j <= t0 + 511 ? hring[(int)(j & (kStRing - 1))] : Rend;
+    };
+    const int64_t rb = hd * a.nblk + block_of(t, a.norm_block, a.nblk);
+    const uint32_t *C = a.cthr + rb * nw;
+    int32_t acc = INT32_MIN;
+    for (int k = 0; k < nw; ++k) acc = max(acc, (int32_t)(Rw(k) - Rt - __ldg(C + k)));
+    if (acc < 0) return -INFINITY;
+    int kb;
+    return stream_exact(Rw, Rt, nw, __ldg(a.m0s + rb), a.coefs + rb * nw, kb);
+}
+
+template <int NW>
+__global__ void __launch_bounds__(256, 4) sps_stream_kernel(BoxcarArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *ring_all = reinterpret_cast<uint32_t *>(smem);
+    float *snr_s = reinterpret_cast<float *>(smem + (size_t)kBxRows * kStRing * 4);
+    int8_t *k_s = reinterpret_cast<int8_t *>(snr_s + kBxRows * kStSS);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = tid >> 4, l = tid & 15;  // staged row of this half-warp, lane in it
+    const int ty = blockIdx.y;
+    const int d0 = ty * kBxIn;
+    const int64_t dr = (int64_t)d0 - 1 + r;
+    const bool present = dr >= 0 && dr < a.ndm;
+    const int32_t *row = present ? a.dmt + dr * a.n_out : nullptr;
+    uint32_t *ring = ring_all + r * kStRing;
+    const int nw = NW > 0 ? NW : a.wl.nw;
+    const int64_t lim = ((1 << 22) - 1) / a.maxw;
+    const int cs = (int)blockIdx.x * kStSeg;
+    const int ce = min(cs + kStSeg, a.n_fast);
+    if (!present)
+        for (int p = l; p < kStSS; p += 16) snr_s[r * kStSS + p] = -INFINITY;
+    // The beam's last chunk(s) go to the tile kernel's list.
+    const int n_tail = (int)((a.n_out + kBxT - 1) / kBxT) - a.n_fast;
+    if (blockIdx.x == gridDim.x - 1 && tid < n_tail) {
+        const int slot = atomicAdd(a.slow_count, 1);
+        a.slow_list[slot] = make_int2(a.n_fast + tid, ty);
+    }
+
+    uint32_t carry = 0;
+    int32_t mnA, mxA, mnB, mxB;  // chunks c and c+1
+    int4 q[4];
+    stream_load(row, cs, l, q);
+    stream_scan(q, cs, ring, l, carry, mnA, mxA);
+    stream_load(row, cs + 1, l, q);
+    stream_scan(q, cs + 1, ring, l, carry, mnB, mxB);
+    bool slow =
+        __syncthreads_or(present && !stream_proof(a, row, dr, cs, l, min(mnA, mnB), max(mxA, mxB), lim));
+
+    for (int c = cs; c < ce; ++c) {
+        const int64_t t0 = (int64_t)c * 256;
+        const int t0m = (int)(t0 & (kStRing - 1));
+        bool any = false;
+        if (!slow) {
+            if (present) {
+                // main points t0 + 64m + 4l + e of this row
+                const int64_t rb = dr * a.nblk + block_of(t0, a.norm_block, a.nblk);
+                const uint32_t *C = a.cthr + rb * nw;
+                uint32_t cw[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) cw[k] = k < nw ? __ldg(C + k) : 0u;
+                float *srow = snr_s + r * kStSS + 4;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int p = 64 * m + 4 * l;
+                    uint4 B;
+                    int32_t acc[4];
+                    stream_prefilter4<NW>(ring, t0m + p, nw, cw, B, acc);
+                    float4 o = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+                    if ((acc[0] & acc[1] & acc[2] & acc[3]) >= 0) {  // some point passes
+                        any = true;
+                        const int32_t m0 = __ldg(a.m0s + rb);
+                        const float2 *cf = a.coefs + rb * nw;
+                        const uint32_t Bv[4] = {B.x, B.y, B.z, B.w};
+                        float ov[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            ov[e] = -INFINITY;
+                            if (acc[e] >= 0) {
+                                const int i = t0m + p + e;
+                                int kb;
+                                ov[e] = stream_exact([&](int k) { return ring[(i + (1 << k)) & (kStRing - 1)]; }, Bv[e],
+                                                     nw, m0, cf, kb);
+                                k_s[r * kStSS + 4 + p + e] = (int8_t)kb;
+                            }
+                        }
+                        o = make_float4(ov[0], ov[1], ov[2], ov[3]);
+                    }
+                    *reinterpret_cast<float4 *>(srow + p) = o;
+                }
+            }
+        } else if (tid == 0) {
+            const int slot = atomicAdd(a.slow_count, 1);
+            a.slow_list[slot] = make_int2(c, ty);
+        }
+        any = __syncthreads_or(any);
+        if (any) {
+            // Halo points t0-1 and t0+256 of all 16 rows (one warp, a point
+            // per lane): needed only where a point passed.
+            if (warp == 0) {
+                const int hr = lane >> 1;
+                const int64_t hd = (int64_t)d0 - 1 + hr;
+                if (hd >= 0 && hd < a.ndm) {
+                    const bool right = lane & 1;
+                    snr_s[hr * kStSS + 4 + (right ? 256 : -1)] = stream_halo(a, ring_all, d0, hr, right, t0, nw);
+                }
+            }
+            __syncthreads();
+            // interior points: threshold, 3x3 rule, append
+            for (int idx = tid; idx < kBxIn * 256; idx += 256) {
+                const int rr = 1 + (idx >> 8), p = idx & 255;
+                const int d = d0 + rr - 1;
+                const float *mid = snr_s + rr * kStSS + 4 + p;
+                const float v = *mid;
+                bool cand = d < a.ndm && v >= a.thr;
+                if (cand) {
+                    const float *up = mid - kStSS, *dn = mid + kStSS;
+                    cand = v > up[-1] && v > up[0] && v > up[1] && v > mid[-1] && v >= mid[1] && v >= dn[-1] &&
+                           v >= dn[0] && v >= dn[1];
+                }
+                const unsigned mask = __ballot_sync(0xffffffffu, cand);
+                if (mask) {
+                    const int leader = __ffs(mask) - 1;
+                    unsigned long long basec = 0;
+                    if (lane == leader) basec = atomicAdd(a.count, (unsigned long long)__popc(mask));
+                    basec = __shfl_sync(0xffffffffu, basec, leader);
+                    if (cand) {
+                        const unsigned long long pos = basec + __popc(mask & ((1u << lane) - 1u));
+                        if ((int64_t)pos < a.cap) {
+                            sp_cand cd;
+                            cd.dm_idx = d;
+                            cd.t = (int32_t)(t0 + p);
+                            cd.width_idx = k_s[rr * kStSS + 4 + p];
+                            cd.snr = v;
+                            a.cands[pos] = cd;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (c + 2 <= ce) {  // chunk c+1 is scored next: bring in chunk c+2
+            mnA = mnB;
+            mxA = mxB;
+            stream_load(row, c + 2, l, q);
+            stream_scan(q, c + 2, ring, l, carry, mnB, mxB);
+            slow = __syncthreads_or(present &&
+                                    !stream_proof(a, row, dr, c + 1, l, min(mnA, mnB), max(mxA, mxB), lim));
+        }
     }
 }
 
@@ -690,17 +1122,20 @@ int64_t sps_nblocks(int64_t n_out, int64_t norm_block) {
     return nb < 1 ? 1 : nb;
 }
 
-// Workspace: per-(row, block) m0, per-(row, block, width) coefficients, and
-// the list of tiles left to the 64-bit pass (count + one entry per tile).
+// Workspace: per-(row, block) m0, per-(row, block, width) coefficients and
+// pre-filter constants, two counters, the tiles the streamed search leaves
+// to the tile kernel and the tiles left to the 64-bit pass (one entry per
+// tile each), and the per-(row, block) sums.
 int64_t sps_workspace_bytes(int32_t ndm, int64_t n_out, int32_t nw, int64_t norm_block) {
     const int64_t nblk = sps_nblocks(n_out, norm_block);
-    return align256((int64_t)ndm * nblk * 4) + align256((int64_t)ndm * nblk * nw * 8) + 256 +
-           align256(boxcar_tiles(ndm, n_out) * 8);
+    return align256((int64_t)ndm * nblk * 4) + align256((int64_t)ndm * nblk * nw * 8) +
+           align256((int64_t)ndm * nblk * nw * 4) + 256 + 2 * align256(boxcar_tiles(ndm, n_out) * 8) +
+           align256((int64_t)ndm * nblk * (int64_t)sizeof(BlockSums));
 }
 
 namespace {
 std::mutex g_sps_lock;
-size_t g_sps_smem[64][4] = {};  // configured boxcar shared memory per (device, kernel)
+size_t g_sps_smem[64][7] = {};  // configured boxcar shared memory per (device, kernel)
 
 template <typename K>
 int configure_kernel(K kernel, int slot, size_t smem) {
@@ -726,6 +1161,9 @@ int configure_boxcar(bool map, int maxw) {
     if (!rc)
         rc = map ? configure_kernel(sps_boxcar_wide_kernel<true>, 2, boxcar_wide_smem(maxw))
                  : configure_kernel(sps_boxcar_wide_kernel<false>, 3, boxcar_wide_smem(maxw));
+    if (!rc && !map) rc = configure_kernel(sps_boxcar_listed_kernel, 4, boxcar_smem(maxw));
+    if (!rc && !map) rc = configure_kernel(sps_stream_kernel<0>, 5, stream_smem());
+    if (!rc && !map) rc = configure_kernel(sps_stream_kernel<9>, 6, stream_smem());
     return rc;
 }
 }  // namespace
@@ -746,16 +1184,31 @@ int launch_sps(const SpsArgs &a, cudaStream_t stream) {
     w8 += align256((int64_t)a.ndm * a.nblk * 4);
     float2 *coefs = reinterpret_cast<float2 *>(w8);
     w8 += align256((int64_t)a.ndm * a.nblk * a.nw * 8);
+    uint32_t *cthr = reinterpret_cast<uint32_t *>(w8);
+    w8 += align256((int64_t)a.ndm * a.nblk * a.nw * 4);
     int *wide_count = reinterpret_cast<int *>(w8);
+    int *slow_count = wide_count + 1;
+    const int64_t ntiles = boxcar_tiles(a.ndm, a.n_out);
     int2 *wide_list = reinterpret_cast<int2 *>(w8 + 256);
+    int2 *slow_list = reinterpret_cast<int2 *>(w8 + 256 + align256(ntiles * 8));
+    BlockSums *sums = reinterpret_cast<BlockSums *>(w8 + 256 + 2 * align256(ntiles * 8));
     const bool map = a.map_best != nullptr;
     int rc = configure_boxcar(map, maxw);
     if (rc) return rc;
+    WidthRoots wr;
+    for (int k = 0; k < SP_MAX_WIDTHS; ++k) {
+        const double w = k < a.nw ? (double)a.widths[k] : 1.0;
+        wr.sw[k] = std::sqrt(w);
+        wr.rsw[k] = 1.0 / std::sqrt(w);
+    }
+    const int64_t nrb = (int64_t)a.ndm * a.nblk;
     sps_stats_kernel<<<dim3((unsigned)a.nblk, (unsigned)a.ndm), 256, 0, stream>>>(a.dmt, a.n_out, a.norm_block,
-                                                                                a.nblk, wl, m0s, coefs);
-    note_launch();
+                                                                                a.nblk, sums);
+    sps_coef_kernel<<<(unsigned)((nrb + 255) / 256), 256, 0, stream>>>(sums, nrb, a.n_out, a.norm_block, a.nblk, wl,
+                                                                      wr, a.threshold, m0s, coefs, cthr);
+    note_launch(2);
     if (cudaGetLastError() != cudaSuccess) return SP_ECUDA;
-    if (cudaMemsetAsync(wide_count, 0, sizeof(int), stream) != cudaSuccess) return SP_ECUDA;
+    if (cudaMemsetAsync(wide_count, 0, 2 * sizeof(int), stream) != cudaSuccess) return SP_ECUDA;
     if (!map && cudaMemsetAsync(a.count, 0, sizeof(int64_t), stream) != cudaSuccess) return SP_ECUDA;
 
     BoxcarArgs b;
@@ -777,7 +1230,12 @@ int launch_sps(const SpsArgs &a, cudaStream_t stream) {
     b.wide_count = wide_count;
     b.wide_list = wide_list;
     b.vec = (a.n_out & 3) == 0 && (reinterpret_cast<uintptr_t>(a.dmt) & 15) == 0;
-    const dim3 grid((unsigned)((a.n_out + kBxT - 1) / kBxT), (unsigned)((a.ndm + kBxIn - 1) / kBxIn));
+    b.n_fast = 0;
+    b.cthr = cthr;
+    b.slow_count = slow_count;
+    b.slow_list = slow_list;
+    const int64_t ntx = (a.n_out + kBxT - 1) / kBxT;
+    const unsigned ngroups = (unsigned)((a.ndm + kBxIn - 1) / kBxIn);
     int nsm = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
                                                   cudaSuccess) {
@@ -785,13 +1243,32 @@ int launch_sps(const SpsArgs &a, cudaStream_t stream) {
         return SP_ECUDA;
     }
     if (map) {
-        sps_boxcar_kernel<true><<<grid, 256, boxcar_smem(maxw), stream>>>(b);
+        sps_boxcar_kernel<true><<<dim3((unsigned)ntx, ngroups), 256, boxcar_smem(maxw), stream>>>(b);
         sps_boxcar_wide_kernel<true><<<nsm, 256, boxcar_wide_smem(maxw), stream>>>(b);
-    } else {
-        sps_boxcar_kernel<false><<<grid, 256, boxcar_smem(maxw), stream>>>(b);
-        sps_boxcar_wide_kernel<false><<<nsm, 256, boxcar_wide_smem(maxw), stream>>>(b);
+        note_launch(2);
+        return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
     }
-    note_launch(2);
+    // Streamed search over the chunks it can take, the tile kernel over the
+    // tiles it lists (the beam's last chunk(s) and the chunks it cannot prove
+    // exact), then the 64-bit pass.
+    bool pow2 = maxw <= 256;
+    for (int k = 0; k < a.nw; ++k) pow2 = pow2 && a.widths[k] == (1 << k);
+    const int64_t n_fast = a.n_out / kBxT - 1;
+    if (pow2 && b.vec && (a.nblk == 1 || a.norm_block % kBxT == 0) && n_fast >= 1 && n_fast <= INT32_MAX) {
+        b.n_fast = (int32_t)n_fast;
+        const dim3 sgrid((unsigned)((n_fast + kStSeg - 1) / kStSeg), ngroups);
+        if (a.nw == 9)  // widths 1..256
+            sps_stream_kernel<9><<<sgrid, 256, stream_smem(), stream>>>(b);
+        else
+            sps_stream_kernel<0><<<sgrid, 256, stream_smem(), stream>>>(b);
+        sps_boxcar_listed_kernel<<<nsm * 4, 256, boxcar_smem(maxw), stream>>>(b);
+        note_launch(2);
+    } else {
+        sps_boxcar_kernel<false><<<dim3((unsigned)ntx, ngroups), 256, boxcar_smem(maxw), stream>>>(b);
+        note_launch();
+    }
+    sps_boxcar_wide_kernel<false><<<nsm, 256, boxcar_wide_smem(maxw), stream>>>(b);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 

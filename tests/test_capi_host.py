@@ -44,8 +44,10 @@ def test_strerror(lib):
 
 
 def test_workspace_sizes(lib):
-    # m0 per (row, block), 9 coefficients per (row, block), the 64-bit tile list (32 x 36 tiles)
-    assert lib.sp_sps_workspace_bytes(501, 8192, 6, 8192) == 2048 + 24064 + 256 + 9216
+    # m0 per (row, block); coefficients and pre-filter constants per (row, block, width); two counters;
+    # the tile lists of the streamed search and of the 64-bit pass (32 x 36 tiles each); 24-byte sums
+    # per (row, block)
+    assert lib.sp_sps_workspace_bytes(501, 8192, 6, 8192) == 2048 + 24064 + 12032 + 256 + 2 * 9216 + 12032
     assert lib.sp_sps_workspace_bytes(0, 10, 1, 0) == -1
 
 

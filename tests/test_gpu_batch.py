@@ -200,11 +200,12 @@ def _held(batch, b):
 def test_batch_graph_replay(mode):
     """Graph replays give the eager results; the launch counter sees the
     eager run's kernels once per replay and none at capture (per beam:
-    staging, block statistics, boxcar, 64-bit boxcar pass; dedispersion once
-    per group, or once per beam with per-beam launches)."""
+    staging, block sums, block coefficients, streamed boxcar, the tile
+    kernel over the tiles it lists, 64-bit boxcar pass; dedispersion once per
+    group, or once per beam with per-beam launches)."""
     batch, plans, plan_dms, f, widths, data, bursts = _small_batch(shape=1)
     s = torch.cuda.Stream()
-    per_step = 5 * batch.nbeams if mode == sp.SP_BATCH_PER_BEAM else 4 * batch.nbeams + batch.ngroups
+    per_step = 7 * batch.nbeams if mode == sp.SP_BATCH_PER_BEAM else 6 * batch.nbeams + batch.ngroups
     with torch.cuda.stream(s):
         lc = sp.launch_count()
         batch.run(mode, stream=s)

@@ -85,8 +85,9 @@ def test_dedisperse_saturated_input():
 
 def test_dedisperse_config1_bitexact():
     """Also counts the kernels: sp_dedisperse launches two (staging,
-    dedispersion), sp_single_pulse_search three (block statistics, boxcar
-    with peaks, 64-bit boxcar pass)."""
+    dedispersion), sp_single_pulse_search five here (block sums, block
+    coefficients, streamed boxcar with peaks, the tile kernel over the tiles
+    it lists, 64-bit boxcar pass)."""
     wl = synth.config1()
     plan = sp.Plan(wl.freqs, wl.tsamp, wl.dms)
     x, _ = synth.make_workload_beam(wl, wl.n_out + plan.max_delay)
@@ -98,7 +99,7 @@ def test_dedisperse_config1_bitexact():
     assert np.array_equal(got, want)
     lc = sp.launch_count()
     gu.dev_candidates(dmt, wl.widths, wl.threshold, wl.norm_block)
-    assert sp.launch_count() - lc == 3
+    assert sp.launch_count() - lc == 5
 
 
 def test_shape_errors():

@@ -73,7 +73,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "real-time beams per GB300; dedispersion G(chan·DM·samp)/s vs roofline"
 MAX_SM_MHZ = 2070.0  # GB300 maximum SM clock
-KERNELS_PER_STEP = 5  # staging, dedispersion, block statistics, boxcar/peaks, 64-bit boxcar pass
 PROFILE_JSON = os.path.join(ROOT, "profiles", "dedisperse_config2_traffic.json")
 DEDISP_SRC = os.path.join(ROOT, "paper_2606_27262_gb300", "csrc", "dedisperse.cu")
 
@@ -409,7 +408,9 @@ def run_ours(args):
                      "peak_basis": f"{nsm} SMs x {lanes:.1f} measured 32-bit add lanes/SM/clk x "
                                    f"{MAX_SM_MHZ:.0f} MHz"},
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
-        "kernels_per_step": KERNELS_PER_STEP,
+        # staging, dedispersion, block sums, block coefficients, streamed
+        # boxcar/peaks, tile kernel over the listed tiles, 64-bit pass
+        "kernels_per_step": launches / args.steps,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

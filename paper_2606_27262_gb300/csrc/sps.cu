@@ -729,7 +729,8 @@ constexpr int kStSS = 264;  // staged S/N row stride: sample t0+p at index 4+p, 
 constexpr int kStSeg = 16;  // chunks per CTA
 
 __host__ __device__ inline size_t stream_smem() {
-    return (size_t)kBxRows * kStRing * 4 + (size_t)kBxRows * kStSS * 4 + (size_t)kBxRows * kStSS;
+    return (size_t)kBxRows * kStRing * 4 + (size_t)kBxRows * kStSS * 4 + (size_t)kBxRows * kStSS +
+           (size_t)kBxRows * 16 * 4;
 }
 
 __device__ __forceinline__ uint4 lds128(const uint32_t *p) { return *reinterpret_cast<const uint4 *>(p); }
@@ -820,7 +821,8 @@ template <typename RW>
 __device__ __forceinline__ float stream_exact(RW Rw, uint32_t Rt, int nw, int32_t m0, const float2 *__restrict__ cf,
                                               int &kbest) {
     float best = -INFINITY;
-    for (int k = 0; k < nw; ++k) {
+#pragma unroll 1
+    for (int k = 0; k < nw; ++k) {  // rare path: kept rolled, so it takes no registers from the hot loop
         const uint32_t w = 1u << k;
         const uint32_t xs = Rw(k) - Rt + (kMagicBits - w * (uint32_t)m0);
         const float2 c = __ldg(cf + k);
@@ -836,7 +838,7 @@ __device__ __forceinline__ float stream_exact(RW Rw, uint32_t Rt, int nw, int32_
 // a[e] = max_k (R[t_e + 2^k] - R[t_e] - C_k) as a 32-bit signed value.  NW
 // widths when NW > 0, else nw (at most 9).
 template <int NW>
-__device__ __forceinline__ void stream_prefilter4(const uint32_t *ring, int i0, int nw, const uint32_t (&cw)[9],
+__device__ __forceinline__ void stream_prefilter4(const uint32_t *ring, int i0, int nw, const uint32_t *cw,
                                                   uint4 &B, int32_t (&a)[4]) {
     const int n = NW > 0 ? NW : nw;
     B = lds128(ring + i0);
@@ -902,6 +904,7 @@ __global__ void __launch_bounds__(256, 4) sps_stream_kernel(BoxcarArgs a) {
     uint32_t *ring_all = reinterpret_cast<uint32_t *>(smem);
     float *snr_s = reinterpret_cast<float *>(smem + (size_t)kBxRows * kStRing * 4);
     int8_t *k_s = reinterpret_cast<int8_t *>(snr_s + kBxRows * kStSS);
+    uint32_t *cw_all = reinterpret_cast<uint32_t *>(k_s + kBxRows * kStSS);  // [16][16] pre-filter constants
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = tid >> 4, l = tid & 15;  // staged row of this half-warp, lane in it
     const int ty = blockIdx.y;
@@ -910,6 +913,7 @@ __global__ void __launch_bounds__(256, 4) sps_stream_kernel(BoxcarArgs a) {
     const bool present = dr >= 0 && dr < a.ndm;
     const int32_t *row = present ? a.dmt + dr * a.n_out : nullptr;
     uint32_t *ring = ring_all + r * kStRing;
+    uint32_t *cw = cw_all + r * 16;
     const int nw = NW > 0 ? NW : a.wl.nw;
     const int64_t lim = ((1 << 22) - 1) / a.maxw;
     const int cs = (int)blockIdx.x * kStSeg;
@@ -937,14 +941,14 @@ __global__ void __launch_bounds__(256, 4) sps_stream_kernel(BoxcarArgs a) {
         const int64_t t0 = (int64_t)c * 256;
         const int t0m = (int)(t0 & (kStRing - 1));
         bool any = false;
-        if (!slow) {
+        if (!slow) {  // uniform across the CTA
+            // the row's pre-filter constants, staged by its own half-warp; the
+            // whole warp meets at the __syncwarp
+            const int64_t rb = present ? dr * a.nblk + block_of(t0, a.norm_block, a.nblk) : 0;
+            if (present && l < nw) cw[l] = __ldg(a.cthr + rb * nw + l);
+            __syncwarp();
             if (present) {
                 // main points t0 + 64m + 4l + e of this row
-                const int64_t rb = dr * a.nblk + block_of(t0, a.norm_block, a.nblk);
-                const uint32_t *C = a.cthr + rb * nw;
-                uint32_t cw[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) cw[k] = k < nw ? __ldg(C + k) : 0u;
                 float *srow = snr_s + r * kStSS + 4;
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {

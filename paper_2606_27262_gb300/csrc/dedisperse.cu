@@ -230,17 +230,22 @@ __device__ __forceinline__ void raster(int64_t id, int ntiles, int64_t ntime, in
 }
 
 // One (DM tile, time tile) of one beam, with DT = the shape's table stride
-// and PACKED = 8 DMs per thread.  Returns false (uniformly across the CTA)
+// and PACKED = 8 DMs per thread; SPLIT (with PACKED) = the warps split the
+// time tile in two halves, so that CH/2 warps of 8 DMs cover a tile of at
+// most 4*CH DMs with the packed sums.  Returns false (uniformly across the CTA)
 // if a staging wait ran out; copies still in flight are waited for (with
 // the same bound) before it returns.
-template <int CH, int SPT, int DT, bool PACKED>
+template <int CH, int SPT, int DT, bool PACKED, bool SPLIT = false>
 __device__ __forceinline__ bool dedisp_tile_body(uint8_t *smem, uint32_t seq0, const uint8_t *__restrict__ xt,
                                                  int64_t pitch, int32_t nchan, int32_t nchunks, int d_first,
                                                  int d_cnt, int64_t t0, const int4 *__restrict__ geo_g,
                                                  const int32_t *__restrict__ off_g, int32_t copies_max,
                                                  int32_t raw_max, int64_t n_out, int32_t *__restrict__ out) {
     using S = Shape<CH, SPT, DT / CH>;
-    constexpr int NDT = PACKED ? 8 : 4, NS = S::NS, NQ = S::NQ, HDR = S::HDR, FLUSH = S::FLUSH;
+    constexpr int NDT = PACKED ? 8 : 4, NS = S::NS, HDR = S::HDR, FLUSH = S::FLUSH;
+    static_assert(!SPLIT || (PACKED && CH % 2 == 0 && S::NQ % 2 == 0), "time split: packed body, even halves");
+    // 4-sample words per lane and row of this warp's share of the time tile
+    constexpr int NQ = SPLIT ? S::NQ / 2 : S::NQ;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);                       // [NS]
     int4 *geo_s = reinterpret_cast<int4 *>(smem + kDedispGeoOffset);           // [NS][CH]
     int32_t *offt_s = reinterpret_cast<int32_t *>(smem + kDedispOffTabOffset);  // [NS][CH*DT]
@@ -249,7 +254,10 @@ __device__ __forceinline__ bool dedisp_tile_body(uint8_t *smem, uint32_t seq0, c
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const bool warp_active = warp * NDT < d_cnt;
+    // DM group and time half of this warp (one half without SPLIT)
+    const int dg = SPLIT ? warp % (CH / 2) : warp;
+    const int th = SPLIT ? warp / (CH / 2) : 0;
+    const bool warp_active = dg * NDT < d_cnt;
     const int4 zero4 = make_int4(0, 0, 0, 0);
 
     auto slot_of = [&](int kk) { return (int)((seq0 + (uint32_t)kk) % NS); };
@@ -354,7 +362,7 @@ __device__ __forceinline__ bool dedisp_tile_body(uint8_t *smem, uint32_t seq0, c
     auto flush = [&](bool first) {
 #pragma unroll
         for (int i = 0; i < NPK; ++i) {
-            const int dl = warp * NDT + i;
+            const int dl = dg * NDT + i;
             if (dl >= d_cnt) continue;
             int32_t *orow = out + (int64_t)(d_first + dl) * n_out;
 #pragma unroll
@@ -363,7 +371,7 @@ __device__ __forceinline__ bool dedisp_tile_body(uint8_t *smem, uint32_t seq0, c
                 const int32_t v0 = (int32_t)(L & 0xFFFFu), v1 = (int32_t)(H & 0xFFFFu);
                 const int32_t v2 = (int32_t)(L >> 16), v3 = (int32_t)(H >> 16);
                 pk[i][q][0] = pk[i][q][1] = 0u;
-                const int64_t t = t0 + 128 * q + 4 * lane;
+                const int64_t t = t0 + 128 * NQ * th + 128 * q + 4 * lane;
                 if (vec && t + 3 < n_out) {
                     int4 *dst = reinterpret_cast<int4 *>(orow + t);
                     int4 cur = first ? zero4 : *dst;
@@ -393,8 +401,8 @@ __device__ __forceinline__ bool dedisp_tile_body(uint8_t *smem, uint32_t seq0, c
             }
         }
         if (warp_active && !failed) {
-            const uint8_t *sb = cop_s + b * copies_max + lane * 4;
-            const int32_t *ot = offt_s + slot_of(k) * CH * DT + warp * NDT;
+            const uint8_t *sb = cop_s + b * copies_max + 128 * NQ * th + lane * 4;
+            const int32_t *ot = offt_s + slot_of(k) * CH * DT + dg * NDT;
             if constexpr (PACKED) {
                 if (nc == CH) {
 #pragma unroll
@@ -488,12 +496,12 @@ __device__ __forceinline__ bool dedisp_tile_body(uint8_t *smem, uint32_t seq0, c
     if constexpr (!PACKED) {
 #pragma unroll
         for (int i = 0; i < NDT; ++i) {
-            const int dl = warp * NDT + i;
+            const int dl = dg * NDT + i;
             if (dl >= d_cnt) continue;
             int32_t *orow = out + (int64_t)(d_first + dl) * n_out;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const int64_t t = t0 + 128 * q + 4 * lane;
+                const int64_t t = t0 + 128 * NQ * th + 128 * q + 4 * lane;
                 if (vec && t + 3 < n_out) {
                     *reinterpret_cast<int4 *>(orow + t) =
                         make_int4(acc[i][4 * q], acc[i][4 * q + 1], acc[i][4 * q + 2], acc[i][4 * q + 3]);
@@ -509,7 +517,9 @@ __device__ __forceinline__ bool dedisp_tile_body(uint8_t *smem, uint32_t seq0, c
 }
 
 // One tile of a shape with NDT DMs per thread: tiles of more than 4*CH DMs
-// take the packed 8-DM body, the others the 4-DM body (same tables).
+// take the packed 8-DM body, the others the packed body with the time tile
+// split between two halves of the warps (same tables); shapes with 4 DMs
+// per thread take the 4-DM body.
 template <int CH, int SPT, int NDT>
 __device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const uint8_t *__restrict__ xt,
                                             int64_t pitch, int32_t nchan, int32_t nchunks, int d_first, int d_cnt,
@@ -521,9 +531,12 @@ __device__ __forceinline__ bool dedisp_tile(uint8_t *smem, uint32_t seq0, const 
         if (d_cnt > 4 * CH)
             return dedisp_tile_body<CH, SPT, DT, true>(smem, seq0, xt, pitch, nchan, nchunks, d_first, d_cnt, t0,
                                                        geo_g, off_g, copies_max, raw_max, n_out, out);
+        return dedisp_tile_body<CH, SPT, DT, true, true>(smem, seq0, xt, pitch, nchan, nchunks, d_first, d_cnt, t0,
+                                                         geo_g, off_g, copies_max, raw_max, n_out, out);
+    } else {
+        return dedisp_tile_body<CH, SPT, DT, false>(smem, seq0, xt, pitch, nchan, nchunks, d_first, d_cnt, t0,
+                                                    geo_g, off_g, copies_max, raw_max, n_out, out);
     }
-    return dedisp_tile_body<CH, SPT, DT, false>(smem, seq0, xt, pitch, nchan, nchunks, d_first, d_cnt, t0, geo_g,
-                                                off_g, copies_max, raw_max, n_out, out);
 }
 
 __device__ __forceinline__ void init_barriers(uint8_t *smem) {

@@ -26,15 +26,22 @@ using namespace sp;
 namespace {
 
 constexpr int kLayers = 5;
+constexpr int kWgradSplitBudget = 304;  // split-K CTAs per weight-gradient GEMM (2 per SM)
 constexpr int kCin[kLayers] = {1, 16, 32, 64, 128};
 constexpr int kCout[kLayers] = {16, 32, 64, 128, 256};
 constexpr int kHin[kLayers] = {256, 128, 64, 32, 16};
 constexpr int kFeat = 256;
+static_assert(kCin[0] == 1 && kCout[0] == 16, "cnn_conv0 computes the one-channel, 16-output first layer");
 constexpr int kAlign = 64;  // parameter segments start at multiples of 64 elements (16-byte aligned bf16)
 
 constexpr int kp_of(int l) { return ((9 * kCin[l] + 31) / 32) * 32; }
 constexpr int ho_of(int l) { return kHin[l] / 2; }
 int64_t up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+// K splits of layer l's weight-gradient GEMM dW [Co][Kp] = dz^T [Co][P] * cols [P][Kp].
+int wgrad_splits(int l, int64_t P) {
+    const int tiles = (int)(((kCout[l] + 127) / 128) * ((kp_of(l) + 63) / 64));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(P / 32, kWgradSplitBudget / tiles));
+}
 
 struct Branch {
     int64_t off_w[kLayers] = {}, off_b[kLayers] = {}, off_hw = 0, off_hb = 0, n = 0;
@@ -53,6 +60,7 @@ struct sp_cnn {
     __nv_bfloat16 *dzT = nullptr, *colsT = nullptr, *wT = nullptr;
     float *dcols = nullptr, *prob = nullptr, *loss = nullptr;
     float *bias_part = nullptr;  // [kBiasChunks][256] partial bias gradients
+    float *wpart = nullptr;      // split-K partials of a weight gradient (summed in order)
     int64_t step = 0;
     bool have_grads = false;
 };
@@ -137,6 +145,7 @@ void free_cnn(sp_cnn *c) {
     cudaFree(c->wT);
     cudaFree(c->dcols);
     cudaFree(c->bias_part);
+    cudaFree(c->wpart);
     cudaFree(c->prob);
     cudaFree(c->loss);
 }
@@ -167,6 +176,14 @@ int forward(sp_cnn *c, const __nv_bfloat16 *ft, const __nv_bfloat16 *dmt, int B,
         for (int l = 0; l < kLayers && !rc; ++l) {
             const int H = kHin[l], Ho = ho_of(l), Kp = kp_of(l);
             const int P = B * Ho * Ho;
+            if (l == 0) {
+                // The first layer directly, without its patch matrix (the
+                // backward pass builds the patches it needs for the weight
+                // gradient), the same in training and inference.
+                rc = cnn_conv0(x, B, H, H, Ho, Ho, b.pb + b.off_w[0], Kp, b.params + b.off_b[0], b.y[0], st);
+                x = b.y[0];
+                continue;
+            }
             rc = cnn_im2col(x, B, H, H, kCin[l], 2, Ho, Ho, Kp, b.cols[l], st);
             if (!rc)
                 rc = cnn_gemm(kEpiBiasRelu, b.cols[l], Kp, b.pb + b.off_w[l], Kp, P, kCout[l], Kp, nullptr, b.y[l],
@@ -182,10 +199,14 @@ int forward(sp_cnn *c, const __nv_bfloat16 *ft, const __nv_bfloat16 *dmt, int B,
     return rc;
 }
 
-int backward(sp_cnn *c, int B, cudaStream_t st) {
+int backward(sp_cnn *c, const __nv_bfloat16 *ft, const __nv_bfloat16 *dmt, int B, cudaStream_t st) {
     int rc = SP_OK;
     for (int bi = 0; bi < 2 && !rc; ++bi) {
         Branch &b = c->br[bi];
+        // the first layer's patches (its forward ran without them)
+        rc = cnn_im2col(bi == 0 ? ft : dmt, B, kHin[0], kHin[0], kCin[0], 2, ho_of(0), ho_of(0), kp_of(0), b.cols[0],
+                        st);
+        if (rc) return rc;
         if (cudaMemsetAsync(b.grads, 0, (size_t)b.n * 4, st) != cudaSuccess) return SP_ECUDA;
         rc = cnn_head_back(b.feat, b.dl, B, kFeat, b.params + b.off_hw, b.dfeat, b.grads + b.off_hw,
                            b.grads + b.off_hb, st);
@@ -198,11 +219,12 @@ int backward(sp_cnn *c, int B, cudaStream_t st) {
             // dW [Co][Kp] = dz^T [Co][P] * cols [P][Kp], split over P.
             if (!rc) rc = cnn_transpose(b.dz[l], P, Co, c->dzT, st);
             if (!rc) rc = cnn_transpose(b.cols[l], P, Kp, c->colsT, st);
-            const int tiles = (int)(((Co + 127) / 128) * ((Kp + 63) / 64));
-            const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(P / 32, 304 / tiles));
+            const int splits = wgrad_splits(l, P);
+            int nz = 0;
             if (!rc)
-                rc = cnn_gemm(kEpiAtomic, c->dzT, P, c->colsT, P, Co, Kp, P, b.grads + b.off_w[l], nullptr, Kp,
-                              nullptr, splits, st);
+                rc = cnn_gemm(kEpiSplit, c->dzT, P, c->colsT, P, Co, Kp, P, c->wpart, nullptr, Kp, nullptr, splits, st,
+                              &nz);
+            if (!rc) rc = cnn_sum_splits(c->wpart, nz, Co, Kp, Kp, b.grads + b.off_w[l], st);
             if (l == 0 || rc) continue;
             // dcols [P][Kp] = dz [P][Co] * W [Co][Kp]; then the gradient of the
             // layer input, masked by the ReLU that produced it.
@@ -272,6 +294,10 @@ extern "C" int sp_cnn_create(int32_t max_batch, uint64_t seed, sp_cnn **out) {
     if (!rc) rc = dalloc((void **)&c->wT, (int64_t)kp_of(kLayers - 1) * kCout[kLayers - 1] * 2);
     if (!rc) rc = dalloc((void **)&c->dcols, dcols_max * 4);
     if (!rc) rc = dalloc((void **)&c->bias_part, (int64_t)kBiasChunks * 256 * 4);
+    int64_t wpart_max = 0;
+    for (int l = 0; l < kLayers; ++l)
+        wpart_max = std::max(wpart_max, (int64_t)wgrad_splits(l, B * ho_of(l) * ho_of(l)) * kCout[l] * kp_of(l));
+    if (!rc) rc = dalloc((void **)&c->wpart, wpart_max * 4);
     if (!rc) rc = dalloc((void **)&c->prob, B * 4);
     if (!rc) rc = dalloc((void **)&c->loss, 4);
     // He-normal convolution weights, zero biases, small head weights.
@@ -361,7 +387,8 @@ extern "C" int sp_cnn_backward(sp_cnn *c, const void *d_ft, const void *d_dmt, c
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     rc = forward(c, static_cast<const __nv_bfloat16 *>(d_ft), static_cast<const __nv_bfloat16 *>(d_dmt), batch,
                  d_labels, c->prob, st);
-    if (!rc) rc = backward(c, batch, st);
+    if (!rc)
+        rc = backward(c, static_cast<const __nv_bfloat16 *>(d_ft), static_cast<const __nv_bfloat16 *>(d_dmt), batch, st);
     if (rc) return rc;
     c->have_grads = true;
     if (h_loss && (cudaMemcpyAsync(h_loss, c->loss, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -389,7 +416,8 @@ extern "C" int sp_cnn_train_step(sp_cnn *c, const void *d_ft, const void *d_dmt,
 }
 
 extern "C" int64_t sp_cnn_features_workspace_bytes(int32_t batch) {
-    return batch > 0 ? 2 * align256((int64_t)batch * kImg * kImg * 4) : -1;
+    // both raw fp32 images and 8 blocks x 4 sums per candidate
+    return batch > 0 ? 2 * align256((int64_t)batch * kImg * kImg * 4) + align256((int64_t)batch * 8 * 16) : -1;
 }
 
 extern "C" int sp_cnn_features(const float *d_sub, int32_t batch, int32_t nsub, int32_t t_in, const int32_t *d_shift,
@@ -401,7 +429,9 @@ extern "C" int sp_cnn_features(const float *d_sub, int32_t batch, int32_t nsub, 
     float *ft_raw = static_cast<float *>(d_work);
     float *dmt_raw = reinterpret_cast<float *>(static_cast<uint8_t *>(d_work) +
                                                align256((int64_t)batch * kImg * kImg * 4));
-    return cnn_features(d_sub, batch, nsub, t_in, d_shift, ft_raw, dmt_raw, static_cast<__nv_bfloat16 *>(d_ft),
+    float *part = reinterpret_cast<float *>(static_cast<uint8_t *>(d_work) +
+                                            2 * align256((int64_t)batch * kImg * kImg * 4));
+    return cnn_features(d_sub, batch, nsub, t_in, d_shift, ft_raw, dmt_raw, part, static_cast<__nv_bfloat16 *>(d_ft),
                         static_cast<__nv_bfloat16 *>(d_dmt), reinterpret_cast<cudaStream_t>(stream));
 }
 

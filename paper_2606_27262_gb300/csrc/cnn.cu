@@ -38,6 +38,9 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool vali
     const int n = valid ? 16 : 0;  // zero-fill outside the matrix
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s_addr(dst)), "l"(src), "r"(n) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s_addr(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -154,8 +157,8 @@ __global__ void __launch_bounds__(256) gemm_nt_kernel(const __nv_bfloat16 *__res
                         Cb[row * ldc + col] = __float2bfloat16(v);
                     } else if (EPI == kEpiStore) {
                         Cf[row * ldc + col] = v;
-                    } else {
-                        atomicAdd(Cf + row * ldc + col, v);
+                    } else {  // this K range's partial product
+                        Cf[(int64_t)blockIdx.z * M * ldc + row * ldc + col] = v;
                     }
                 }
             }
@@ -202,6 +205,48 @@ __global__ void im2col_c1_kernel(const __nv_bfloat16 *__restrict__ x, int H, int
         dst[0] = *reinterpret_cast<const uint4 *>(&v[0]);
         dst[1] = *reinterpret_cast<const uint4 *>(&v[8]);
         for (uint32_t j = 2; j < kp_chunks; ++j) dst[j] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Layer 0 of the inference forward (one input channel, 3x3, stride 2, zero
+// padding 1) as a direct convolution: one thread per output pixel gathers
+// its nine taps and accumulates the sixteen outputs in fp32 from the bf16
+// weights (every product exact), then adds the bias, applies the ReLU and
+// rounds once to bf16 -- the im2col + GEMM path's result up to the order of
+// its fp32 accumulation, without writing and reading the patch matrix.
+constexpr int kConv0Out = 16;
+__global__ void __launch_bounds__(256) conv0_kernel(const __nv_bfloat16 *__restrict__ x, int H, int W, int Ho,
+                                                    int Wo, uint32_t P, const __nv_bfloat16 *__restrict__ w, int Kp,
+                                                    const float *__restrict__ bias, __nv_bfloat16 *__restrict__ y) {
+    __shared__ float ws[kConv0Out][9];
+    __shared__ float bs[kConv0Out];
+    if (threadIdx.x < kConv0Out * 9) {
+        const int co = threadIdx.x / 9, k = threadIdx.x - co * 9;
+        ws[co][k] = __bfloat162float(w[co * Kp + k]);
+    }
+    if (threadIdx.x < kConv0Out) bs[threadIdx.x] = bias[threadIdx.x];
+    __syncthreads();
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;  // one pixel per thread (the grid covers P)
+    if (p < P) {
+        const uint32_t t = p / (uint32_t)Wo, wo = p - t * (uint32_t)Wo;
+        const uint32_t n = t / (uint32_t)Ho, ho = t - n * (uint32_t)Ho;
+        float v[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int h = 2 * (int)ho - 1 + k / 3, ww = 2 * (int)wo - 1 + k % 3;
+            v[k] = (h >= 0 && h < H && ww >= 0 && ww < W) ? __bfloat162float(x[((size_t)n * H + h) * W + ww]) : 0.f;
+        }
+        __align__(16) __nv_bfloat16 o[kConv0Out];
+#pragma unroll
+        for (int co = 0; co < kConv0Out; ++co) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc = fmaf(v[k], ws[co][k], acc);
+            o[co] = __float2bfloat16(fmaxf(acc + bs[co], 0.f));
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(y + (size_t)p * kConv0Out);
+        dst[0] = *reinterpret_cast<const uint4 *>(&o[0]);
+        dst[1] = *reinterpret_cast<const uint4 *>(&o[8]);
     }
 }
 
@@ -299,6 +344,18 @@ __global__ void col2im_relu_vec_kernel(const float *__restrict__ dcols, const __
 #pragma unroll
         for (int e = 0; e < 8; ++e) o[e] = __float2bfloat16(__bfloat162float(xb[e]) > 0.f ? s[e] : 0.f);
         *reinterpret_cast<uint4 *>(dz + (size_t)pix * C + c0) = *reinterpret_cast<const uint4 *>(o);
+    }
+}
+
+// C[i][j] += the nz split partials of element (i, j), added in split order.
+__global__ void sum_splits_kernel(const float *__restrict__ part, int nz, int M, int N, int64_t ldc,
+                                  float *__restrict__ C) {
+    const int64_t total = (int64_t)M * N, zs = (int64_t)M * ldc;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / N, j = e - i * N, o = i * ldc + j;
+        float a = 0.f;
+        for (int z = 0; z < nz; ++z) a += part[z * zs + o];
+        C[o] += a;
     }
 }
 
@@ -463,72 +520,127 @@ __global__ void to_bf16_kernel(const float *__restrict__ a, int64_t n, __nv_bflo
 // shift[j][k]] (bins outside the spectrum count 0), u0 = (T_in - 256) / 2.
 // One CTA per (block of kFeatRows rows j, candidate), one thread per bin u:
 // subband k's whole row of T_in bins is staged in shared memory (double
-// buffered) and serves the CTA's kFeatRows shifted sums at once, with the
-// block's shift table transposed beside it.  (A third buffer with the next
-// row prefetched into registers ran at half the speed: fewer CTAs per SM.)
+// buffered) between kImg zero bins on each side and serves the CTA's
+// kFeatRows shifted sums at once.  Each shift is clamped once, when the
+// block's shift table is staged, to [-u0 - kImg, T_in - u0]: a row whose
+// window lies wholly outside the spectrum then reads only zeros, so the sum
+// loop needs no bounds test; per subband a thread takes its kFeatRows shifts
+// with 16-byte broadcast loads; the next subband's row is fetched by
+// asynchronous copies (cp.async) while the current one is summed.  (A third
+// buffer with the next row prefetched into registers ran at half the speed:
+// fewer CTAs per SM.)
 constexpr int kFeatRows = 32;
 __global__ void __launch_bounds__(kImg) features_raw_kernel(const float *__restrict__ sub, int T_in,
                                                             const int32_t *__restrict__ shift,
-                                                            float *__restrict__ ft_raw, float *__restrict__ dmt_raw) {
+                                                            float *__restrict__ ft_raw, float *__restrict__ dmt_raw,
+                                                            float4 *__restrict__ part) {
     extern __shared__ __align__(16) float fsm[];
-    float *rows = fsm;                                          // [2][T_in]
-    int32_t *sh = reinterpret_cast<int32_t *>(fsm + 2 * T_in);  // [kImg subbands][kFeatRows]
+    // staged row: kImg zeros, T_in bins, kImg zeros (stride a multiple of 4 floats, so that the shift
+    // table after the two rows is 16-byte aligned for its int4 loads)
+    const int RW = (T_in + 2 * kImg + 3) & ~3;
+    float *rows = fsm;                                          // [2][RW]
+    int32_t *sh = reinterpret_cast<int32_t *>(fsm + 2 * RW);    // [kImg subbands][kFeatRows]
     const int b = blockIdx.y, j0 = blockIdx.x * kFeatRows, u = threadIdx.x;
     const int u0 = (T_in - kImg) / 2;
     const float *sb = sub + (size_t)b * kImg * T_in;
-    for (int r = 0; r < kFeatRows; ++r)
-        ft_raw[((size_t)b * kImg + j0 + r) * kImg + u] = sb[(size_t)(j0 + r) * T_in + u0 + u];
+    float fs = 0.f, fs2 = 0.f;  // this thread's share of the block's frequency-time sums
+    for (int r = 0; r < kFeatRows; ++r) {
+        const float v = sb[(size_t)(j0 + r) * T_in + u0 + u];
+        ft_raw[((size_t)b * kImg + j0 + r) * kImg + u] = v;
+        fs += v;
+        fs2 += v * v;
+    }
     for (int i = threadIdx.x; i < kImg * kFeatRows; i += blockDim.x) {
         const int r = i / kImg, k = i - r * kImg;
-        sh[k * kFeatRows + r] = shift[(size_t)(j0 + r) * kImg + k];
+        sh[k * kFeatRows + r] = min(max(shift[(size_t)(j0 + r) * kImg + k], -u0 - kImg), T_in - u0);
     }
-    for (int i = threadIdx.x; i < T_in; i += blockDim.x) rows[i] = sb[i];
+    for (int i = threadIdx.x; i < kImg; i += blockDim.x) {  // the zero margins of both buffers
+        rows[i] = rows[kImg + T_in + i] = 0.f;
+        rows[RW + i] = rows[RW + kImg + T_in + i] = 0.f;
+    }
+    for (int i = 2 * kImg + T_in + threadIdx.x; i < RW; i += blockDim.x) rows[i] = rows[RW + i] = 0.f;
+    for (int i = threadIdx.x; i < T_in; i += blockDim.x) rows[kImg + i] = sb[i];
     __syncthreads();
     float acc[kFeatRows];
 #pragma unroll
     for (int r = 0; r < kFeatRows; ++r) acc[r] = 0.f;
     for (int k = 0; k < kImg; ++k) {
-        const float *cur = rows + (k & 1) * T_in;
-        float *nxt = rows + ((k + 1) & 1) * T_in;  // read last in step k - 1, before its barrier
-        if (k + 1 < kImg)
-            for (int i = threadIdx.x; i < T_in; i += blockDim.x) nxt[i] = sb[(size_t)(k + 1) * T_in + i];
-        const int32_t *shk = sh + k * kFeatRows;
-#pragma unroll
-        for (int r = 0; r < kFeatRows; ++r) {
-            const int t = u0 + u + shk[r];
-            if ((unsigned)t < (unsigned)T_in) acc[r] += cur[t];
+        // bin u + shift of the row lies at index kImg + u0 + u + shift
+        const float *cur = rows + (k & 1) * RW + kImg + u0 + u;
+        float *nxt = rows + ((k + 1) & 1) * RW + kImg;  // read last in step k - 1, before its barrier
+        // the next row arrives by asynchronous copies while this one is summed
+        if (k + 1 < kImg) {
+            for (int i = threadIdx.x; i < T_in; i += blockDim.x) cp_async4(nxt + i, sb + (size_t)(k + 1) * T_in + i);
+            cp_async_commit();
         }
+        const int4 *shk = reinterpret_cast<const int4 *>(sh + k * kFeatRows);
+#pragma unroll
+        for (int q = 0; q < kFeatRows / 4; ++q) {
+            const int4 s4 = shk[q];
+            acc[4 * q] += cur[s4.x];
+            acc[4 * q + 1] += cur[s4.y];
+            acc[4 * q + 2] += cur[s4.z];
+            acc[4 * q + 3] += cur[s4.w];
+        }
+        cp_async_wait<0>();
         __syncthreads();
     }
+    float ds = 0.f, ds2 = 0.f;
 #pragma unroll
-    for (int r = 0; r < kFeatRows; ++r) dmt_raw[((size_t)b * kImg + j0 + r) * kImg + u] = acc[r];
+    for (int r = 0; r < kFeatRows; ++r) {
+        dmt_raw[((size_t)b * kImg + j0 + r) * kImg + u] = acc[r];
+        ds += acc[r];
+        ds2 += acc[r] * acc[r];
+    }
+    // The block's sums of both images, in a fixed order: warp trees, then
+    // the warps in turn (the normalisation adds the blocks in turn).
+    float4 t4 = make_float4(fs, fs2, ds, ds2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t4.x += __shfl_xor_sync(0xffffffffu, t4.x, o);
+        t4.y += __shfl_xor_sync(0xffffffffu, t4.y, o);
+        t4.z += __shfl_xor_sync(0xffffffffu, t4.z, o);
+        t4.w += __shfl_xor_sync(0xffffffffu, t4.w, o);
+    }
+    __shared__ float4 wsum[kImg / 32];
+    if ((u & 31) == 0) wsum[u >> 5] = t4;
+    __syncthreads();
+    if (u == 0) {
+        float4 a = wsum[0];
+        for (int w = 1; w < kImg / 32; ++w) {
+            a.x += wsum[w].x;
+            a.y += wsum[w].y;
+            a.z += wsum[w].z;
+            a.w += wsum[w].w;
+        }
+        part[(size_t)b * (kImg / kFeatRows) + blockIdx.x] = a;
+    }
 }
 
-__global__ void normalise_kernel(const float *__restrict__ raw, __nv_bfloat16 *__restrict__ out) {
-    const int64_t base = (int64_t)blockIdx.x * kImg * kImg;
+// One CTA per (block of kFeatRows rows, candidate, image): the image's mean
+// and population variance from the feature kernel's per-block sums (added
+// in block order), then the block's rows scaled and stored as bf16.
+__global__ void __launch_bounds__(kImg) normalise_kernel(const float *__restrict__ ft_raw,
+                                                         const float *__restrict__ dmt_raw,
+                                                         const float4 *__restrict__ part, __nv_bfloat16 *__restrict__ ft,
+                                                         __nv_bfloat16 *__restrict__ dmt) {
+    const int b = blockIdx.y, img = blockIdx.z, j0 = blockIdx.x * kFeatRows, u = threadIdx.x;
     float s = 0.f, s2 = 0.f;
-    for (int i = threadIdx.x; i < kImg * kImg; i += blockDim.x) {
-        const float v = raw[base + i];
-        s += v;
-        s2 += v * v;
-    }
-    __shared__ float r1[256], r2[256];
-    r1[threadIdx.x] = s;
-    r2[threadIdx.x] = s2;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o; o >>= 1) {
-        if ((int)threadIdx.x < o) {
-            r1[threadIdx.x] += r1[threadIdx.x + o];
-            r2[threadIdx.x] += r2[threadIdx.x + o];
-        }
-        __syncthreads();
+    for (int q = 0; q < kImg / kFeatRows; ++q) {
+        const float4 p = part[(size_t)b * (kImg / kFeatRows) + q];
+        s += img ? p.z : p.x;
+        s2 += img ? p.w : p.y;
     }
     const float n = (float)(kImg * kImg);
-    const float mean = r1[0] / n;
-    const float var = fmaxf(r2[0] / n - mean * mean, 0.f);
+    const float mean = s / n;
+    const float var = fmaxf(s2 / n - mean * mean, 0.f);
     const float inv = var > 0.f ? rsqrtf(var) : 0.f;
-    for (int i = threadIdx.x; i < kImg * kImg; i += blockDim.x)
-        out[base + i] = __float2bfloat16((raw[base + i] - mean) * inv);
+    const float *raw = img ? dmt_raw : ft_raw;
+    __nv_bfloat16 *out = img ? dmt : ft;
+    for (int r = 0; r < kFeatRows; ++r) {
+        const size_t i = ((size_t)b * kImg + j0 + r) * kImg + u;
+        out[i] = __float2bfloat16((raw[i] - mean) * inv);
+    }
 }
 
 // Subband dynamic spectrum of candidate q from the staged beam xt
@@ -569,21 +681,30 @@ int grid_for(int64_t n, int threads = 256) {
 }  // namespace
 
 int cnn_gemm(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int M, int N,
-             int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st) {
+             int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st,
+             int *nz_out) {
     // the tensor cores (tcgen05) where the shapes suit them
-    const int rc = cnn_gemm_tc(epi, A, lda, B, ldb, M, N, K, Cf, Cb, ldc, bias, splits, st);
+    const int rc = cnn_gemm_tc(epi, A, lda, B, ldb, M, N, K, Cf, Cb, ldc, bias, splits, st, nz_out);
     if (rc != SP_ELIMIT) return rc;
     if (K % kBK) return SP_EINVAL;
-    if (splits < 1) splits = 1;
+    if (splits < 1 || epi != kEpiSplit) splits = 1;
     int64_t ks = ((K / kBK + splits - 1) / splits) * kBK;
     const int nz = (int)((K + ks - 1) / ks);
+    if (nz_out) *nz_out = nz;
     const dim3 grid((unsigned)((N + kBN - 1) / kBN), (unsigned)((M + kBM - 1) / kBM), (unsigned)nz);
     if (epi == kEpiBiasRelu)
         gemm_nt_kernel<kEpiBiasRelu><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, ks, Cf, Cb, ldc, bias);
-    else if (epi == kEpiStore && nz == 1)
+    else if (epi == kEpiStore)
         gemm_nt_kernel<kEpiStore><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, ks, Cf, Cb, ldc, bias);
     else
-        gemm_nt_kernel<kEpiAtomic><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, ks, Cf, Cb, ldc, bias);
+        gemm_nt_kernel<kEpiSplit><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, ks, Cf, Cb, ldc, bias);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_sum_splits(const float *part, int nz, int M, int N, int64_t ldc, float *C, cudaStream_t st) {
+    if (nz < 1) return SP_EINVAL;
+    sum_splits_kernel<<<grid_for((int64_t)M * N), 256, 0, st>>>(part, nz, M, N, ldc, C);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
@@ -602,6 +723,15 @@ int cnn_im2col(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, 
     } else {
         im2col_kernel<<<grid_for(P * Kp), 256, 0, st>>>(x, Nb, H, W, C, stride, Ho, Wo, Kp, cols);
     }
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int cnn_conv0(const __nv_bfloat16 *x, int Nb, int H, int W, int Ho, int Wo, const __nv_bfloat16 *w, int Kp,
+              const float *bias, __nv_bfloat16 *y, cudaStream_t st) {
+    const int64_t P = (int64_t)Nb * Ho * Wo;
+    if (P >= ((int64_t)1 << 31) || Kp < 9 || (reinterpret_cast<uintptr_t>(y) & 15)) return SP_ELIMIT;
+    conv0_kernel<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(x, H, W, Ho, Wo, (uint32_t)P, w, Kp, bias, y);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
@@ -696,19 +826,18 @@ int cnn_extract(const uint8_t *xt, int64_t pitch, int64_t n_in, int32_t nchan, c
 }
 
 int cnn_features(const float *sub, int Nb, int S, int T_in, const int32_t *shift, float *ft_raw, float *dmt_raw,
-                 __nv_bfloat16 *ft, __nv_bfloat16 *dmt, cudaStream_t st) {
+                 float *part, __nv_bfloat16 *ft, __nv_bfloat16 *dmt, cudaStream_t st) {
     if (S != kImg || T_in < kImg || T_in > 4096) return SP_EINVAL;
-    const size_t smem = (size_t)2 * T_in * 4 + (size_t)kImg * kFeatRows * 4;  // <= 32 KB + 32 KB
+    const size_t smem = (size_t)2 * ((T_in + 2 * kImg + 3) & ~3) * 4 + (size_t)kImg * kFeatRows * 4;  // <= 36 KB + 32 KB
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(features_raw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return SP_ECUDA;
-    features_raw_kernel<<<dim3(kImg / kFeatRows, Nb), kImg, smem, st>>>(sub, T_in, shift, ft_raw, dmt_raw);
+    float4 *p4 = reinterpret_cast<float4 *>(part);
+    features_raw_kernel<<<dim3(kImg / kFeatRows, Nb), kImg, smem, st>>>(sub, T_in, shift, ft_raw, dmt_raw, p4);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return SP_ECUDA;
-    normalise_kernel<<<Nb, 256, 0, st>>>(ft_raw, ft);
-    note_launch();
-    normalise_kernel<<<Nb, 256, 0, st>>>(dmt_raw, dmt);
+    normalise_kernel<<<dim3(kImg / kFeatRows, Nb, 2), kImg, 0, st>>>(ft_raw, dmt_raw, p4, ft, dmt);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }

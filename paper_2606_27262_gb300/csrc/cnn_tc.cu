@@ -185,9 +185,12 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
                 for (int j = 0; j < 4; ++j)
                     dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
                                          __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
-            } else {
+            } else {  // this K range's partial product
+                float4 *dst = reinterpret_cast<float4 *>(Cf + (int64_t)blockIdx.z * M * ldc + (int64_t)row * ldc + col);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) atomicAdd(Cf + (int64_t)row * ldc + col + j, __uint_as_float(v[j]));
+                for (int j = 0; j < 4; ++j)
+                    dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                         __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
             }
         }
     } else if (!ok && threadIdx.x == 0) {
@@ -280,7 +283,8 @@ int dispatch_bn(int bn, const CUtensorMap &ta, const CUtensorMap &tb, int M, int
 // Tensor-core GEMM; SP_ELIMIT when the shapes do not suit it (the caller then
 // uses the mma.sync kernel).
 int cnn_gemm_tc(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int M, int N,
-                int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st) {
+                int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st,
+                int *nz_out) {
     if (M < 64 || N % 16 || N < 16 || K <= 0 || lda % 8 || ldb % 8 || ldc % 8 ||
         (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
         return SP_ELIMIT;
@@ -291,14 +295,15 @@ int cnn_gemm_tc(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
     CUtensorMap ta, tb;
     if (!make_map(&ta, A, M, K, lda, kTcBM) || !make_map(&tb, B, N, K, ldb, bn)) return SP_ELIMIT;
     const int kbt = (int)((K + kTcBK - 1) / kTcBK);
-    if (splits < 1 || epi != kEpiAtomic) splits = 1;
+    if (splits < 1 || epi != kEpiSplit) splits = 1;
     const int kps = (kbt + splits - 1) / splits;
     const int nz = (kbt + kps - 1) / kps;
+    if (nz_out) *nz_out = nz;
     if (epi == kEpiBiasRelu)
         return dispatch_bn<kEpiBiasRelu>(bn, ta, tb, M, N, kps, kbt, nz, Cf, Cb, ldc, bias, st);
     if (epi == kEpiStore)
         return dispatch_bn<kEpiStore>(bn, ta, tb, M, N, kps, kbt, nz, Cf, Cb, ldc, bias, st);
-    return dispatch_bn<kEpiAtomic>(bn, ta, tb, M, N, kps, kbt, nz, Cf, Cb, ldc, bias, st);
+    return dispatch_bn<kEpiSplit>(bn, ta, tb, M, N, kps, kbt, nz, Cf, Cb, ldc, bias, st);
 }
 
 int cnn_gemm_tc_status(int *h_status, bool clear) {

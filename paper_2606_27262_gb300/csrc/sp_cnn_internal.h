@@ -9,22 +9,33 @@
 namespace sp {
 
 constexpr int kImg = 256;  // images are kImg x kImg (subbands or trial DMs x time bins)
-constexpr int kEpiBiasRelu = 0, kEpiStore = 1, kEpiAtomic = 2;
+constexpr int kEpiBiasRelu = 0, kEpiStore = 1, kEpiSplit = 2;
 
 // C[M,N] = A[M,K] * B[N,K]^T (bf16, row-major, K % 32 == 0).  kEpiBiasRelu:
-// Cb = bf16(relu(C + bias)); kEpiStore: Cf = C; kEpiAtomic: Cf += C (with
-// `splits` K ranges in parallel; Cf zeroed by the caller).
+// Cb = bf16(relu(C + bias)); kEpiStore: Cf = C; kEpiSplit: at most `splits`
+// K ranges in parallel, range z storing its partial product to
+// Cf + z*M*ldc (*nz_out receives how many ran; cnn_sum_splits adds them up
+// in order, so the result does not depend on scheduling).
 int cnn_gemm(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int M, int N,
-             int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st);
+             int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st,
+             int *nz_out = nullptr);
+// C[i][j] += sum over z < nz, in order, of part[z][i][j] (M x N, row stride ldc).
+int cnn_sum_splits(const float *part, int nz, int M, int N, int64_t ldc, float *C, cudaStream_t st);
 // The same product on the tensor cores (tcgen05, TMEM accumulator, TMA
 // operands; cnn_tc.cu): any K (zero past K), N a multiple of 16, M >= 64,
 // 16-byte aligned rows; SP_ELIMIT when a shape does not suit it.
 int cnn_gemm_tc(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int M, int N,
-                int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st);
+                int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st,
+                int *nz_out);
 // Device status of the tensor-core GEMMs (bit 0: a wait ran out).
 int cnn_gemm_tc_status(int *h_status, bool clear);
 int cnn_im2col(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho, int Wo, int Kp,
                __nv_bfloat16 *cols, cudaStream_t st);
+// Layer 0 (one input channel, 16 outputs, 3x3, stride 2, padding 1) as a
+// direct convolution with bias and ReLU: y [Nb*Ho*Wo][16] bf16 (16-byte
+// aligned), weights w [16][Kp] bf16 (taps 0..8 used), bias [16] fp32.
+int cnn_conv0(const __nv_bfloat16 *x, int Nb, int H, int W, int Ho, int Wo, const __nv_bfloat16 *w, int Kp,
+              const float *bias, __nv_bfloat16 *y, cudaStream_t st);
 int cnn_col2im_relu(const float *dcols, const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho,
                     int Wo, int Kp, __nv_bfloat16 *dz, cudaStream_t st);
 int cnn_transpose(const __nv_bfloat16 *in, int64_t R, int64_t C, __nv_bfloat16 *out, cudaStream_t st);
@@ -51,7 +62,8 @@ struct ExtractWidths {
 int cnn_extract(const uint8_t *xt, int64_t pitch, int64_t n_in, int32_t nchan, const int32_t *delays,
                 const sp_cand *cands, int32_t ncand, const ExtractWidths &wt, int32_t nsub, int32_t t_in, float *sub,
                 cudaStream_t st);
+// part: Nb * 8 float4 of workspace (per-block image sums, 16-byte aligned).
 int cnn_features(const float *sub, int Nb, int S, int T_in, const int32_t *shift, float *ft_raw, float *dmt_raw,
-                 __nv_bfloat16 *ft, __nv_bfloat16 *dmt, cudaStream_t st);
+                 float *part, __nv_bfloat16 *ft, __nv_bfloat16 *dmt, cudaStream_t st);
 
 }  // namespace sp

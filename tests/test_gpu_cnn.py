@@ -53,6 +53,22 @@ def test_features_parity():
         assert np.all(np.abs(g - o) <= 2 ** -7 * np.abs(o) + 2e-3)
 
 
+def test_features_parity_odd_length_and_wide_shifts():
+    """An odd spectrum length (301 bins) and a shift table whose sweep (600
+    bins) carries rows wholly outside the spectrum: bins outside count 0."""
+    rng = np.random.default_rng(3)
+    sub = torch.from_numpy(rng.normal(0.0, 1.0, size=(3, 256, 301)).astype(np.float32)).cuda()
+    shift = sp.dmt_shifts(FREQS, 256, 600)
+    assert shift.min() < -(301 - 256) // 2 - 256 and shift.max() > 301
+    ft = torch.empty((3, 256, 256), dtype=torch.bfloat16, device="cuda")
+    dmt = torch.empty_like(ft)
+    sp.cnn_features(sub, torch.from_numpy(shift).cuda(), ft, dmt)
+    torch.cuda.synchronize()
+    oft, odmt = ocnn.features(sub.cpu().numpy().astype(np.float64), shift)
+    for g, o in ((_as64(ft), oft), (_as64(dmt), odmt)):
+        assert np.all(np.abs(g - o) <= 2 ** -7 * np.abs(o) + 2e-3)
+
+
 def test_forward_gradients_and_adam_vs_oracle():
     rng = np.random.default_rng(1)
     B = 4

@@ -140,3 +140,35 @@ def test_non_pow2_widths_use_the_tile_kernel():
     _check(dmt, [1, 3, 5, 17], 0, (3.0,), streamed=False)
     _check(dmt, sp_widths(512), 0, (3.0,), streamed=False)  # widths past 256
     _check(dmt, sp_widths(32), 1000, (3.0,), streamed=False)  # blocks not a multiple of 256
+
+
+def test_stream_threshold_at_exact_values():
+    """Thresholds set exactly to S/N values the library computes: a 3x3 peak
+    whose best S/N equals the threshold is a candidate (v >= thr), so the
+    pre-filter's bound must let every such window through.  The values come
+    from the best-S/N map, whose tile kernel evaluates the same expression as
+    the streamed kernel's exact path on these noise rows."""
+    rng = np.random.default_rng(21)
+    ndm, n_out = 20, 3 * 256 + 40
+    dmt = _noise(rng, ndm, n_out)
+    _plant_pulses(dmt, rng, [100, 300, 520])
+    gb, _ = gu.dev_best_map(torch.from_numpy(dmt).cuda(), sp_widths(256), 0)
+    fin = np.where(np.isfinite(gb), gb, -np.inf)
+    pad = np.pad(fin, 1, constant_values=-np.inf)
+    # strict 3x3 maxima (no ties) in the streamed chunks (t < 512)
+    nb = np.stack([pad[1 + a: 1 + a + ndm, 1 + b: 1 + b + n_out] for a in (-1, 0, 1) for b in (-1, 0, 1)
+                   if a or b])
+    peak = (fin > nb.max(axis=0)) & np.isfinite(fin)
+    peak[:, 512:] = False
+    d_idx, t_idx = np.nonzero(peak)
+    order = np.argsort(-fin[d_idx, t_idx])
+    picks = [(int(d_idx[i]), int(t_idx[i])) for i in order[:: max(1, order.size // 12)][:12]]
+    assert len(picks) >= 6
+    for d, t in picks:
+        thr = float(gb[d, t])
+        g, n, kernels = _search(dmt, sp_widths(256), thr, 0)
+        assert kernels == 5
+        found = {(int(a), int(b)): float(v) for a, b, v in zip(g["dm_idx"], g["t"], g["snr"])}
+        assert (d, t) in found, (d, t, thr)
+        assert found[(d, t)] == np.float32(thr)
+        assert all(v >= np.float32(thr) for v in found.values())

@@ -106,6 +106,8 @@ def parse_args(argv=None):
     p.add_argument("--dmt-budget-gb", type=float, default=24.0,
                    help="batched workload: DM-transform bytes per group arena (GB)")
     p.add_argument("--no-per-beam", action="store_true", help="batched workload: skip the comparisons")
+    p.add_argument("--cls-infer-only", action="store_true",
+                   help="classifier workload: skip the training phase (for profiling the inference step)")
     p.add_argument("--batch-mode", choices=["persistent", "grid"], default="grid",
                    help="batched workload: dedispersion launch style of the timed step (grid: one CTA per "
                         "work item; persistent: a resident grid draining a work queue)")
@@ -972,19 +974,23 @@ def run_classifier(args):
         sp.cnn_features(sub, shift, ft[:bt], dmt[:bt], work)
         clf.train_step(ft[:bt], dmt[:bt], labels[k % len(pool)], 1e-3)
 
-    for k in range(max(args.warmup, 3)):
-        train_step(k)
-    torch.cuda.synchronize(dev)
-    steps = max(args.steps, 1) * 40
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    e0.record(stream)
-    for k in range(steps):
-        train_step(k)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    train_ms = e0.elapsed_time(e1) / steps
+    steps, train_ms = 0, None
+    if not args.cls_infer_only:
+        for k in range(max(args.warmup, 3)):
+            train_step(k)
+        torch.cuda.synchronize(dev)
+        steps = max(args.steps, 1) * 40
+        clocks.start()
+        e0.record(stream)
+        for k in range(steps):
+            train_step(k)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        train_ms = e0.elapsed_time(e1) / steps
+    else:
+        clocks.start()
     # inference: features + forward on batches of 256 candidates
     big = scls.classifier_batch(rng, bi, freqs, device=dev)[0]
     prob = torch.empty(bi, device=dev)
@@ -1004,7 +1010,7 @@ def run_classifier(args):
     infer_ms = e0.elapsed_time(e1) / reps
     clk = clocks.stop()
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1900.0)
-    tr_tflops = cnn_flops_per_example(True) * bt / (train_ms / 1e3) / 1e12
+    tr_tflops = cnn_flops_per_example(True) * bt / (train_ms / 1e3) / 1e12 if train_ms else None
     in_tflops = cnn_flops_per_example(False) * bi / (infer_ms / 1e3) / 1e12
     line = {
         "metric": "classifier candidates per second (inference) and training examples per second",
@@ -1015,11 +1021,11 @@ def run_classifier(args):
                                "images, 0.79 M parameters", "batch_infer": bi, "batch_train": bt,
                    "params": int(sp.library().sp_cnn_num_params())},
         "training": {"examples_per_s": bt / (train_ms / 1e3), "ms_per_step": train_ms, "steps": steps,
-                     "tflops": tr_tflops},
+                     "tflops": tr_tflops} if train_ms else None,
         "roofline": {"bound": "tensor", "achieved": in_tflops, "peak": peak, "unit": "TFLOP/s",
                      "frac": in_tflops / peak, "traffic": None,
-                     "kernel": "inference step (features + im2col + gemm_nt_kernel + pooling/head), algorithmic "
-                               "convolution FLOPs over the step time",
+                     "kernel": "inference step (features, first layer, im2col + tcgen05 GEMMs, pooling/head), "
+                               "algorithmic convolution FLOPs over the step time",
                      "peak_basis": "measured bf16 GEMM burst (MEASURED_PEAKS.json)"},
         "e2e": None, "cpu_baseline": None, "clocks": clk, "gpu_launches": launches,
     }

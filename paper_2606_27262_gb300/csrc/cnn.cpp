@@ -176,12 +176,18 @@ int forward(sp_cnn *c, const __nv_bfloat16 *ft, const __nv_bfloat16 *dmt, int B,
         for (int l = 0; l < kLayers && !rc; ++l) {
             const int H = kHin[l], Ho = ho_of(l), Kp = kp_of(l);
             const int P = B * Ho * Ho;
-            if (l == 0) {
-                // The first layer directly, without its patch matrix (the
-                // backward pass builds the patches it needs for the weight
-                // gradient), the same in training and inference.
+            // No patch matrix in the forward pass (the backward pass builds the
+            // patches it needs for the weight gradients), the same in training
+            // and inference: the first layer directly, the others as implicit
+            // GEMMs on the tensor cores, or im2col + GEMM where a shape does not
+            // suit those.
+            if (l == 0)
                 rc = cnn_conv0(x, B, H, H, Ho, Ho, b.pb + b.off_w[0], Kp, b.params + b.off_b[0], b.y[0], st);
-                x = b.y[0];
+            else
+                rc = cnn_conv_tc(x, B, H, H, kCin[l], Ho, Ho, b.pb + b.off_w[l], Kp, kCout[l], b.params + b.off_b[l],
+                                 b.y[l], st);
+            if (rc != SP_ELIMIT) {
+                x = b.y[l];
                 continue;
             }
             rc = cnn_im2col(x, B, H, H, kCin[l], 2, Ho, Ho, Kp, b.cols[l], st);
@@ -203,10 +209,7 @@ int backward(sp_cnn *c, const __nv_bfloat16 *ft, const __nv_bfloat16 *dmt, int B
     int rc = SP_OK;
     for (int bi = 0; bi < 2 && !rc; ++bi) {
         Branch &b = c->br[bi];
-        // the first layer's patches (its forward ran without them)
-        rc = cnn_im2col(bi == 0 ? ft : dmt, B, kHin[0], kHin[0], kCin[0], 2, ho_of(0), ho_of(0), kp_of(0), b.cols[0],
-                        st);
-        if (rc) return rc;
+
         if (cudaMemsetAsync(b.grads, 0, (size_t)b.n * 4, st) != cudaSuccess) return SP_ECUDA;
         rc = cnn_head_back(b.feat, b.dl, B, kFeat, b.params + b.off_hw, b.dfeat, b.grads + b.off_hw,
                            b.grads + b.off_hb, st);
@@ -216,6 +219,10 @@ int backward(sp_cnn *c, const __nv_bfloat16 *ft, const __nv_bfloat16 *dmt, int B
             const int Ho = ho_of(l), Kp = kp_of(l), Co = kCout[l];
             const int64_t P = (int64_t)B * Ho * Ho;
             rc = cnn_bias_grad(b.dz[l], P, Co, b.grads + b.off_b[l], c->bias_part, st);
+            // the layer's patches (the forward pass ran without them)
+            if (!rc)
+                rc = cnn_im2col(l == 0 ? (bi == 0 ? ft : dmt) : b.y[l - 1], B, kHin[l], kHin[l], kCin[l], 2, Ho, Ho, Kp,
+                                b.cols[l], st);
             // dW [Co][Kp] = dz^T [Co][P] * cols [P][Kp], split over P.
             if (!rc) rc = cnn_transpose(b.dz[l], P, Co, c->dzT, st);
             if (!rc) rc = cnn_transpose(b.cols[l], P, Kp, c->colsT, st);

@@ -4,7 +4,7 @@
 //
 //   C[M,N] = A[M,K] * B[N,K]^T, bf16 operands (both K-major, rows of
 //   lda / ldb elements), fp32 accumulate; epilogue bias + ReLU -> bf16,
-//   fp32 store, or fp32 atomic add (split K).
+//   fp32 store, or a split-K partial product.
 //
 // One CTA of 4 warps computes a 128 x BN tile (BN = 16..256, a multiple of
 // 16): warp 0 streams K blocks of 64 of A (128 x 64) and B (BN x 64) into a
@@ -16,6 +16,11 @@
 // four warps read their 32 accumulator rows from tensor memory
 // (tcgen05.ld) and apply the epilogue.  Every wait is bounded; a wait that
 // runs out skips the epilogue and sets the status word.
+//
+// Convolutions with short K (cnn_conv_tc) run as implicit GEMMs: A's rows are
+// output pixels' 3x3 patches, gathered by warps 2 and 3 from the NHWC input
+// straight into the swizzled shared-memory layout (two stages, so that more
+// CTAs share an SM), and no patch matrix is written to global memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -68,13 +73,53 @@ __device__ __forceinline__ bool mbar_wait_tc(uint32_t bar, uint32_t parity) {
     return true;
 }
 
-template <int EPI, int BN>
+// Implicit-GEMM convolution geometry (3x3, stride 2, zero padding 1): A's
+// row p is output pixel p = (n, ho, wo) of an NHWC bf16 input x [Nb][H][W][C],
+// column k = tap * C + c with tap = 3 * ky + kx -- the layout of the im2col
+// matrix, never written out.  C, Ho and Wo are powers of two (shifts).
+struct ConvGeom {
+    const __nv_bfloat16 *x;
+    int H, W;
+    int lc, lwo, lho;  // log2 of C, Wo, Ho
+};
+
+// One stage's A tile (128 rows x 64 columns of K) gathered by the 64 threads
+// of warps 2 and 3 into the 128-byte-swizzled K-major layout that the TMA
+// copies produce: 16-byte chunk j of row r at chunk j ^ (r & 7) of the
+// row's 128 bytes.  Taps past the ninth and pixels outside the image are
+// zeros.
+__device__ __forceinline__ void gather_a(const ConvGeom &g, int M, int m0, int k0, uint8_t *sa, int t) {
+    const int C = 1 << g.lc;
+    uint4 v[16];  // all sixteen loads in flight before the first store
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int cid = t + 64 * q, r = cid >> 3, j = cid & 7;
+        const int k = k0 + 8 * j, tap = k >> g.lc, c0 = k & (C - 1), p = m0 + r;
+        v[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (p < M && tap < 9) {
+            const int wo = p & ((1 << g.lwo) - 1), t2 = p >> g.lwo;
+            const int ho = t2 & ((1 << g.lho) - 1), n = t2 >> g.lho;
+            const int h = 2 * ho - 1 + tap / 3, w = 2 * wo - 1 + tap % 3;
+            if (h >= 0 && h < g.H && w >= 0 && w < g.W)
+                v[q] = __ldg(reinterpret_cast<const uint4 *>(g.x + (((int64_t)n * g.H + h) * g.W + w) * C + c0));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int cid = t + 64 * q, r = cid >> 3, j = cid & 7;
+        *reinterpret_cast<uint4 *>(sa + r * 128 + ((j ^ (r & 7)) << 4)) = v[q];
+    }
+}
+
+template <int EPI, int BN, bool GATHER = false>
 __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, int M, int N,
                                                       int kb_per_split, int kb_total, float *__restrict__ Cf,
                                                       __nv_bfloat16 *__restrict__ Cb, int64_t ldc,
-                                                      const float *__restrict__ bias) {
+                                                      const float *__restrict__ bias, ConvGeom geom) {
     constexpr int A_BYTES = kTcBM * kTcBK * 2, B_BYTES = BN * kTcBK * 2, STAGE = A_BYTES + B_BYTES;
+    // gathered A: two stages, so that more CTAs (and gathering warps) fit on an SM
+    constexpr int kTcStages = GATHER ? 2 : sp::kTcStages;
     constexpr int NCOL = BN < 32 ? 32 : BN;  // tensor-memory columns: a power of two >= 32
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256 && (NCOL & (NCOL - 1)) == 0, "MMA N");
     extern __shared__ uint8_t smem_raw[];
@@ -95,7 +140,8 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
     }
     if (threadIdx.x == 32) {
         for (int s = 0; s < kTcStages; ++s) {
-            mbar_init_tc(full0 + 8 * s, 1);
+            // gathered A: the B copy's arrival plus one per gathering warp
+            mbar_init_tc(full0 + 8 * s, GATHER ? 3 : 1);
             mbar_init_tc(empty0 + 8 * s, 1);
         }
         mbar_init_tc(done, 1);
@@ -113,14 +159,17 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
             if (i >= kTcStages) ok = mbar_wait_tc(empty0 + 8 * s, ((i / kTcStages) - 1) & 1);
             if (!ok) break;
             const uint32_t fb = full0 + 8 * s;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE) : "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                         "r"(GATHER ? B_BYTES : STAGE)
+                         : "memory");
             const int k0 = (kb_lo + i) * kTcBK;
             uint8_t *sa = smem + s * STAGE;
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                "[%4];" ::"r"(s_addr32(sa)),
-                "l"(&tmA), "r"(k0), "r"(m0), "r"(fb)
-                : "memory");
+            if (!GATHER)
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                    "%3}], [%4];" ::"r"(s_addr32(sa)),
+                    "l"(&tmA), "r"(k0), "r"(m0), "r"(fb)
+                    : "memory");
             asm volatile(
                 "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
                 "[%4];" ::"r"(s_addr32(sa + A_BYTES)),
@@ -150,6 +199,21 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
         if (ok)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
                          : "memory");
+    } else if (GATHER && warp >= 2) {  // A gatherers: warps 2 and 3
+        for (int i = 0; i < kb_n && ok; ++i) {
+            const int s = i % kTcStages;
+            if (i >= kTcStages) {  // the stage's last MMAs have read it (lane 0 waits, the warp follows)
+                int w_ok = 1;
+                if (lane == 0) w_ok = mbar_wait_tc(empty0 + 8 * s, ((i / kTcStages) - 1) & 1);
+                ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+                if (!ok) break;
+            }
+            gather_a(geom, M, m0, (kb_lo + i) * kTcBK, smem + s * STAGE, threadIdx.x - 64);
+            // generic-proxy stores, read next by the tensor cores' async proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full0 + 8 * s) : "memory");
+        }
     }
     // Everyone waits for the last MMA (a role that gave up lets the wait run out).
     if (kb_n > 0) ok = mbar_wait_tc(done, 0) && ok;
@@ -202,9 +266,10 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL) : "memory");
 }
 
-template <int EPI, int BN>
+template <int EPI, int BN, bool GATHER = false>
 constexpr int tc_smem_bytes() {
-    return 1024 + kTcStages * (kTcBM * kTcBK * 2 + BN * kTcBK * 2) + 8 * (2 * kTcStages + 1) + 16;
+    constexpr int S = GATHER ? 2 : kTcStages;
+    return 1024 + S * (kTcBM * kTcBK * 2 + BN * kTcBK * 2) + 8 * (2 * S + 1) + 16;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -238,10 +303,11 @@ bool make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t rows, int64_t c
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int EPI, int BN>
+template <int EPI, int BN, bool GATHER = false>
 int launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int kb_per_split, int kb_total, int nz,
-              float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, cudaStream_t st) {
-    constexpr int smem = tc_smem_bytes<EPI, BN>();
+              float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, cudaStream_t st,
+              const ConvGeom &geom = ConvGeom{}) {
+    constexpr int smem = tc_smem_bytes<EPI, BN, GATHER>();
     static std::mutex lock;
     static bool configured[64] = {};
     int dev = 0;
@@ -252,7 +318,8 @@ int launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int kb
     {
         std::lock_guard<std::mutex> guard(lock);
         if (!configured[dev]) {
-            if (cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            if (cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN, GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem) !=
                 cudaSuccess) {
                 cudaGetLastError();
                 return SP_ECUDA;
@@ -261,7 +328,8 @@ int launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int kb
         }
     }
     const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kTcBM - 1) / kTcBM), (unsigned)nz);
-    gemm_tc_kernel<EPI, BN><<<grid, 128, smem, st>>>(ta, tb, M, N, kb_per_split, kb_total, Cf, Cb, ldc, bias);
+    gemm_tc_kernel<EPI, BN, GATHER>
+        <<<grid, 128, smem, st>>>(ta, tb, M, N, kb_per_split, kb_total, Cf, Cb, ldc, bias, geom);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? SP_OK : SP_ECUDA;
 }
@@ -304,6 +372,48 @@ int cnn_gemm_tc(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
     if (epi == kEpiStore)
         return dispatch_bn<kEpiStore>(bn, ta, tb, M, N, kps, kbt, nz, Cf, Cb, ldc, bias, st);
     return dispatch_bn<kEpiSplit>(bn, ta, tb, M, N, kps, kbt, nz, Cf, Cb, ldc, bias, st);
+}
+
+// 3x3 stride-2 convolution (zero padding 1) with bias and ReLU as an implicit
+// GEMM on the tensor cores: y [Nb*Ho*Wo][N] = relu(patches(x) * w^T + bias),
+// the patches gathered into shared memory by the kernel.  SP_ELIMIT when the
+// shapes do not suit it (the caller then uses im2col + cnn_gemm).
+int cnn_conv_tc(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int Ho, int Wo, const __nv_bfloat16 *w, int Kp,
+                int N, const float *bias, __nv_bfloat16 *y, cudaStream_t st) {
+    auto lg = [](int v) {
+        int l = 0;
+        while ((1 << l) < v) ++l;
+        return (1 << l) == v ? l : -1;
+    };
+    const int lc = lg(C), lwo = lg(Wo), lho = lg(Ho);
+    const int64_t M = (int64_t)Nb * Ho * Wo;
+    // Long K (9C > 576: the 128-channel layer) keeps more stages in flight with TMA copies of a
+    // written patch matrix than two stages of gathered patches do: left to im2col + cnn_gemm.
+    if (lc < 3 || 9 * C > 576 || lwo < 0 || lho < 0 || H != 2 * Ho || W != 2 * Wo || M < 64 || M > INT32_MAX ||
+        N % 16 || N < 16 ||
+        N > 256 || Kp < 9 * C || Kp % 8 || !bias || (reinterpret_cast<uintptr_t>(x) & 15) ||
+        (reinterpret_cast<uintptr_t>(w) & 15) || (reinterpret_cast<uintptr_t>(y) & 15))
+        return SP_ELIMIT;
+    const int bn = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+    CUtensorMap tb;
+    if (!make_map(&tb, w, N, 9 * C, Kp, bn)) return SP_ELIMIT;
+    const int kbt = (9 * C + kTcBK - 1) / kTcBK;
+    ConvGeom g;
+    g.x = x;
+    g.H = H;
+    g.W = W;
+    g.lc = lc;
+    g.lwo = lwo;
+    g.lho = lho;
+    switch (bn) {  // the A map is unused with gathered A
+        case 16: return launch_tc<kEpiBiasRelu, 16, true>(tb, tb, (int)M, N, kbt, kbt, 1, nullptr, y, N, bias, st, g);
+        case 32: return launch_tc<kEpiBiasRelu, 32, true>(tb, tb, (int)M, N, kbt, kbt, 1, nullptr, y, N, bias, st, g);
+        case 64: return launch_tc<kEpiBiasRelu, 64, true>(tb, tb, (int)M, N, kbt, kbt, 1, nullptr, y, N, bias, st, g);
+        case 128:
+            return launch_tc<kEpiBiasRelu, 128, true>(tb, tb, (int)M, N, kbt, kbt, 1, nullptr, y, N, bias, st, g);
+        default:
+            return launch_tc<kEpiBiasRelu, 256, true>(tb, tb, (int)M, N, kbt, kbt, 1, nullptr, y, N, bias, st, g);
+    }
 }
 
 int cnn_gemm_tc_status(int *h_status, bool clear) {

@@ -27,6 +27,13 @@ int cnn_sum_splits(const float *part, int nz, int M, int N, int64_t ldc, float *
 int cnn_gemm_tc(int epi, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int M, int N,
                 int64_t K, float *Cf, __nv_bfloat16 *Cb, int64_t ldc, const float *bias, int splits, cudaStream_t st,
                 int *nz_out);
+// 3x3 stride-2 convolution (zero padding 1) + bias + ReLU as an implicit GEMM
+// on the tensor cores (patches gathered into shared memory, no im2col
+// matrix): x NHWC bf16 [Nb][H][W][C], w [N][Kp] bf16 (k = tap*C + c), y
+// [Nb*Ho*Wo][N] bf16.  C, Ho, Wo powers of two, 8 <= C <= 64, H = 2 Ho,
+// W = 2 Wo; SP_ELIMIT when a shape does not suit it.
+int cnn_conv_tc(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int Ho, int Wo, const __nv_bfloat16 *w, int Kp,
+                int N, const float *bias, __nv_bfloat16 *y, cudaStream_t st);
 // Device status of the tensor-core GEMMs (bit 0: a wait ran out).
 int cnn_gemm_tc_status(int *h_status, bool clear);
 int cnn_im2col(const __nv_bfloat16 *x, int Nb, int H, int W, int C, int stride, int Ho, int Wo, int Kp,

@@ -49,6 +49,9 @@ def test_workspace_sizes(lib):
     # per (row, block)
     assert lib.sp_sps_workspace_bytes(501, 8192, 6, 8192) == 2048 + 24064 + 12032 + 256 + 2 * 9216 + 12032
     assert lib.sp_sps_workspace_bytes(0, 10, 1, 0) == -1
+    # classifier features: both raw fp32 images per candidate and 8 blocks x 4 fp32 sums per candidate
+    assert lib.sp_cnn_features_workspace_bytes(3) == 2 * 786432 + 512
+    assert lib.sp_cnn_features_workspace_bytes(0) == -1
 
 
 def test_argument_checks_need_no_gpu(lib):

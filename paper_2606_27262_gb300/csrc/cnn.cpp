@@ -209,7 +209,6 @@ int backward(sp_cnn *c, const __nv_bfloat16 *ft, const __nv_bfloat16 *dmt, int B
     int rc = SP_OK;
     for (int bi = 0; bi < 2 && !rc; ++bi) {
         Branch &b = c->br[bi];
-
         if (cudaMemsetAsync(b.grads, 0, (size_t)b.n * 4, st) != cudaSuccess) return SP_ECUDA;
         rc = cnn_head_back(b.feat, b.dl, B, kFeat, b.params + b.off_hw, b.dfeat, b.grads + b.off_hw,
                            b.grads + b.off_hb, st);
@@ -219,7 +218,8 @@ int backward(sp_cnn *c, const __nv_bfloat16 *ft, const __nv_bfloat16 *dmt, int B
             const int Ho = ho_of(l), Kp = kp_of(l), Co = kCout[l];
             const int64_t P = (int64_t)B * Ho * Ho;
             rc = cnn_bias_grad(b.dz[l], P, Co, b.grads + b.off_b[l], c->bias_part, st);
-            // the layer's patches (the forward pass ran without them)
+            // the layer's patches (the forward pass writes them only where it
+            // falls back to im2col)
             if (!rc)
                 rc = cnn_im2col(l == 0 ? (bi == 0 ? ft : dmt) : b.y[l - 1], B, kHin[l], kHin[l], kCin[l], 2, Ho, Ho, Kp,
                                 b.cols[l], st);

@@ -118,19 +118,19 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
                                                       __nv_bfloat16 *__restrict__ Cb, int64_t ldc,
                                                       const float *__restrict__ bias, ConvGeom geom) {
     constexpr int A_BYTES = kTcBM * kTcBK * 2, B_BYTES = BN * kTcBK * 2, STAGE = A_BYTES + B_BYTES;
-    // gathered A: two stages, so that more CTAs (and gathering warps) fit on an SM
-    constexpr int kTcStages = GATHER ? 2 : sp::kTcStages;
+    // stages of the ring; gathered A: two, so that more CTAs (and gathering warps) fit on an SM
+    constexpr int NS = GATHER ? 2 : kTcStages;
     constexpr int NCOL = BN < 32 ? 32 : BN;  // tensor-memory columns: a power of two >= 32
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256 && (NCOL & (NCOL - 1)) == 0, "MMA N");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024 - (s_addr32(smem_raw) & 1023)) & 1023);  // swizzle atoms 1024-aligned
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kTcStages * STAGE);   // full[S], empty[S], done
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kTcStages + 1);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * STAGE);   // full[S], empty[S], done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NS + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
     const int kb_lo = blockIdx.z * kb_per_split;
     const int kb_n = min(kb_total, kb_lo + kb_per_split) - kb_lo;
-    const uint32_t full0 = s_addr32(bars), empty0 = s_addr32(bars + kTcStages), done = s_addr32(bars + 2 * kTcStages);
+    const uint32_t full0 = s_addr32(bars), empty0 = s_addr32(bars + NS), done = s_addr32(bars + 2 * NS);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr32(tmem_slot)),
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 32) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             // gathered A: the B copy's arrival plus one per gathering warp
             mbar_init_tc(full0 + 8 * s, GATHER ? 3 : 1);
             mbar_init_tc(empty0 + 8 * s, 1);
@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
 
     if (warp == 0 && lane == 0) {  // producer: K blocks into the stage ring
         for (int i = 0; i < kb_n && ok; ++i) {
-            const int s = i % kTcStages;
-            if (i >= kTcStages) ok = mbar_wait_tc(empty0 + 8 * s, ((i / kTcStages) - 1) & 1);
+            const int s = i % NS;
+            if (i >= NS) ok = mbar_wait_tc(empty0 + 8 * s, ((i / NS) - 1) & 1);
             if (!ok) break;
             const uint32_t fb = full0 + 8 * s;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
         }
     } else if (warp == 1 && lane == 0) {  // MMA issuer
         for (int i = 0; i < kb_n && ok; ++i) {
-            const int s = i % kTcStages;
-            ok = mbar_wait_tc(full0 + 8 * s, (i / kTcStages) & 1);
+            const int s = i % NS;
+            ok = mbar_wait_tc(full0 + 8 * s, (i / NS) & 1);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = s_addr32(smem + s * STAGE), sb = sa + A_BYTES;
@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const __grid_constant__ CU
                          : "memory");
     } else if (GATHER && warp >= 2) {  // A gatherers: warps 2 and 3
         for (int i = 0; i < kb_n && ok; ++i) {
-            const int s = i % kTcStages;
-            if (i >= kTcStages) {  // the stage's last MMAs have read it (lane 0 waits, the warp follows)
+            const int s = i % NS;
+            if (i >= NS) {  // the stage's last MMAs have read it (lane 0 waits, the warp follows)
                 int w_ok = 1;
-                if (lane == 0) w_ok = mbar_wait_tc(empty0 + 8 * s, ((i / kTcStages) - 1) & 1);
+                if (lane == 0) w_ok = mbar_wait_tc(empty0 + 8 * s, ((i / NS) - 1) & 1);
                 ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
                 if (!ok) break;
             }

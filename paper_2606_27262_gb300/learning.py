@@ -187,7 +187,7 @@ def harvest_beams(h: Harvester, make_beam, seeds, beam) -> Harvest:
     return Harvest(torch.cat(fts), torch.cat(dms), np.concatenate(labs), beams, n_cands)
 
 
-def judge(p: np.ndarray, hv: Harvest, snr_min: float = 8.0, p_min: float = 0.5) -> dict:
+def assess(p: np.ndarray, hv: Harvest, snr_min: float = 8.0, p_min: float = 0.5) -> dict:
     """Recall and false positives of probabilities p (one per kept peak of
     ``hv``): a burst injected at S/N >= snr_min counts as kept when the
     sifter kept a peak on it, and as accepted when one of those peaks has

@@ -73,7 +73,7 @@ def test_training_set_has_both_classes(pipeline):
 def test_classifier_on_pipeline_candidates(pipeline):
     plan, clf, _, test_set, _ = pipeline
     p = learning.classify(clf, test_set.ft, test_set.dm_img)
-    j = learning.judge(p, test_set)
+    j = learning.assess(p, test_set)
     print(f"pipeline candidates of {TEST_BEAMS} held-out beams: {j['candidates']} found, {j['kept_peaks']} kept "
           f"by the sifter; bursts S/N >= 8: {j['injected']} injected, {j['kept']} kept, {j['accepted']} accepted "
           f"(recall {j['recall']:.4f}); non-burst peaks passed: sifter alone {j['fp_sifter']}, "
